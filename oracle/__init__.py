@@ -1,0 +1,22 @@
+"""FP64 CPU oracle for GMF-FLBM on D3Q27 (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
+reference leg may import this package.  The product library never links or
+calls it; it shares no code, header or table with the CUDA path.
+
+Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
+
+* ``tables``            pinned: Table II printed b_k, orthogonality, n_k/mu_k relation
+* ``philox4x32_10``     pinned: published known-answer vectors (Salmon et al. SC'11)
+* ``normals``           pinned: moments of the normal stream; Box-Muller identity
+* ``feq2``              pinned: moments 0/1/2 exact, zero ghost projection
+* ``noise_term``        pinned: conservation, single-node AR(1) stationary variance
+* ``collide_node/step`` pinned: conservation, AR(1) lag-1 = 1-omega / 0, shear-wave
+                        viscosity, tau=1 GMF == BGK, kT=0 cube-rotation covariance
+* ``REG`` scheme        parity unpinned for its ghost relaxation (the paper does
+                        not define Reg-FLBM's ghost non-equilibrium treatment);
+                        its full-order equilibrium coefficients are pinned against
+                        the product-form D3Q27 equilibrium
+* ``structure_factor``  pinned: numpy FFT, Parseval, single-plane-wave shell
+"""
+from .oracle import *  # noqa: F401,F403

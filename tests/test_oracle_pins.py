@@ -1,0 +1,453 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test pins one part of the oracle to something other than the oracle
+itself: a value printed in the paper (Tables I/II, golden fixtures), a
+published known-answer vector, an exact identity, a closed form, or a special
+case that reduces to a library routine.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from synth import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+CS2 = 1.0 / 3.0
+
+
+def _read(name):
+    rows = []
+    with open(os.path.join(GOLD, name)) as fh:
+        for ln in fh:
+            ln = ln.strip()
+            if ln and not ln.startswith("#"):
+                rows.append(ln.split())
+    return rows
+
+
+# --------------------------------------------------------------------------
+# Tables I and II
+
+
+def test_table1_velocity_set_and_weights(oracle_mod):
+    T = oracle_mod.tables()
+    c, w = T["c"], T["w"]
+    assert len({tuple(v) for v in c}) == 27
+    assert np.all(np.abs(c) <= 1)
+    for s, count, wt in _read("table1_weights_D3Q27.txt"):
+        sel = (c ** 2).sum(1) == int(s)
+        assert sel.sum() == int(count)
+        assert np.allclose(w[sel], float(Fraction(wt)), rtol=0, atol=1e-17)
+    # isotropy of the weights: sum w = 1, sum w c c = c_s^2 delta
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.allclose((w[:, None, None] * c[:, :, None] * c[:, None, :]).sum(0),
+                       CS2 * np.eye(3), atol=1e-16)
+    # opposite velocities adjacent (layout reading): c_{i+1} = -c_i for odd i
+    for i in range(1, 27, 2):
+        assert np.all(c[i + 1] == -c[i])
+
+
+def test_table2_printed_bk_and_orthogonality(oracle_mod):
+    """Sum_i w_i e_ki e_li = b_k delta_kl with b_k as printed in Table II."""
+    T = oracle_mod.tables()
+    E, w, b = T["E"], T["w"], T["b"]
+    rows = _read("table2_hermite_D3Q27.txt")
+    printed_b = np.array([float(Fraction(r[4])) for r in rows])
+    printed_n = np.array([int(r[2]) for r in rows])
+    printed_mu = np.array([int(r[3]) for r in rows])
+    assert np.array_equal(T["nk"], printed_n)
+    assert np.array_equal(T["muk"], printed_mu)
+    assert np.allclose(b, printed_b, rtol=1e-15, atol=0)
+    G = (E * w) @ E.T
+    assert np.abs(G - np.diag(printed_b)).max() < 1e-15
+    # round trip: f -> moments -> f with f_i = w_i sum_k e_ki m_k / b_k
+    f = inputs.normal_field(27, seed=7)
+    m = E @ f
+    f2 = w * (E.T @ (m / printed_b))
+    assert np.abs(f2 - f).max() < 1e-14
+
+
+def test_table2_symbols_match_polynomials(oracle_mod):
+    """Each e_ki of the oracle is the polynomial the Table II symbol names:
+    prod over axes of p_deg(c_a), p0=1, p1=c, p2=c^2-c_s^2."""
+    T = oracle_mod.tables()
+    E, c = T["E"], T["c"].astype(float)
+    p = [lambda v: np.ones_like(v), lambda v: v, lambda v: v * v - CS2]
+    for r in _read("table2_hermite_D3Q27.txt"):
+        k, sym = int(r[0]), r[1]
+        deg = [0, 0, 0]
+        if sym != "1":
+            i = 0
+            while i < len(sym):
+                ax = "xyz".index(sym[i])
+                if i + 1 < len(sym) and sym[i + 1] == "2":
+                    deg[ax] += 2
+                    i += 2
+                else:
+                    deg[ax] += 1
+                    i += 1
+            if sym in ("xx", "yy", "zz"):
+                deg = [2 if d else 0 for d in deg]
+        expect = p[deg[0]](c[:, 0]) * p[deg[1]](c[:, 1]) * p[deg[2]](c[:, 2])
+        assert np.abs(E[k] - expect).max() < 1e-15, (k, sym)
+
+
+# --------------------------------------------------------------------------
+# Random numbers
+
+
+def test_philox_known_answers(oracle_mod):
+    for r in _read("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in r]
+        out = oracle_mod.philox4x32_10(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_normals_box_muller_mapping(oracle_mod):
+    """r_k^2 + r_{k+1}^2 = -2 ln u1 of the matching Philox word pair (block j
+    word m feeds mode 4+4j+m), and r_27 is dropped."""
+    seed, node, step = 0x1234_5678_9ABC, 77, (1 << 33) + 5
+    r = oracle_mod.normals(seed, node, step)
+    assert np.all(r[:4] == 0)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for j in range(6):
+        o = oracle_mod.philox4x32_10([node, step & 0xFFFFFFFF, j, step >> 32], key)
+        for p in range(2):
+            k = 4 + 4 * j + 2 * p
+            u1 = ((int(o[2 * p]) >> 9) + 0.5) / 2 ** 23
+            u2 = ((int(o[2 * p + 1]) >> 9) + 0.5) / 2 ** 23
+            rad2 = -2 * np.log(u1)
+            if k + 1 <= 26:
+                assert abs(r[k] ** 2 + r[k + 1] ** 2 - rad2) < 1e-12 * max(1, rad2)
+                assert abs(np.arctan2(r[k + 1], r[k]) % (2 * np.pi) - 2 * np.pi * u2) < 1e-9
+            else:
+                assert abs(abs(r[k]) - np.sqrt(rad2) * abs(np.cos(2 * np.pi * u2))) < 1e-12
+
+
+def test_normals_are_standard_normal(oracle_mod):
+    from scipy import stats
+    draws = np.array([oracle_mod.normals(99, n, s)[4:]
+                      for n in range(400) for s in range(25)]).ravel()
+    assert abs(draws.mean()) < 4 / np.sqrt(draws.size)
+    assert abs(draws.var() - 1) < 4 * np.sqrt(2 / draws.size)
+    assert stats.kstest(draws, "norm").pvalue > 1e-3
+
+
+# --------------------------------------------------------------------------
+# Equilibrium, noise, conservation
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_feq2_moments_and_zero_ghosts(oracle_mod, seed):
+    T = oracle_mod.tables()
+    E, c = T["E"], T["c"].astype(float)
+    rng = np.random.default_rng(seed)
+    rho = 0.8 + 0.4 * rng.random()
+    u = 0.1 * rng.standard_normal(3)
+    f = oracle_mod.feq2(rho, u)
+    assert abs(f.sum() - rho) < 1e-15
+    assert np.abs(c.T @ f - rho * u).max() < 1e-15
+    H2 = c[:, :, None] * c[:, None, :] - CS2 * np.eye(3)
+    assert np.abs(np.einsum("i,iab->ab", f, H2) - rho * np.outer(u, u)).max() < 1e-15
+    assert np.abs(E[10:] @ f).max() < 1e-15
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+def test_noise_conserves_mass_and_momentum(oracle_mod, scheme):
+    T = oracle_mod.tables()
+    c = T["c"].astype(float)
+    for node in range(20):
+        r = oracle_mod.normals(5, node, 3)
+        xi = oracle_mod.noise_term(scheme, 0.8, 1e-2, 1.1, r)
+        assert abs(xi.sum()) < 1e-16
+        assert np.abs(c.T @ xi).max() < 1e-16
+        assert np.abs(xi).max() > 1e-4
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+def test_collision_conserves(oracle_mod, scheme):
+    T = oracle_mod.tables()
+    c, w = T["c"].astype(float), T["w"]
+    f = w * (1.0 + 0.05 * inputs.normal_field(27, seed=scheme + 10))
+    fs = oracle_mod.collide_node(scheme, 0.7, 1e-3, f, seed=3, node=11, step=4)
+    assert abs(fs.sum() - f.sum()) < 1e-15
+    assert np.abs(c.T @ fs - c.T @ f).max() < 1e-15
+
+
+def test_box_mass_momentum_drift(oracle_mod):
+    """Global mass and momentum are constant to roundoff on a periodic box
+    (drift <= 1e-12 M(0) after 200 steps from a perturbed state)."""
+    T = oracle_mod.tables()
+    c, w = T["c"].astype(float), T["w"]
+    nx, ny, nz = 7, 6, 5
+    box = oracle_mod.Box(nx, ny, nz, tau=0.8, kT=1e-4, seed=1234)
+    f0 = w[:, None, None, None] * (1 + 0.01 * inputs.population_perturbation(nx, ny, nz, 3))
+    box.set_f(f0)
+    M0 = f0.sum()
+    P0 = np.einsum("ia,ixyz->a", c, f0)
+    box.step(200)
+    f = box.get_f()
+    assert abs(f.sum() - M0) <= 1e-12 * M0
+    assert np.abs(np.einsum("ia,ixyz->a", c, f) - P0).max() <= 1e-12 * M0
+
+
+# --------------------------------------------------------------------------
+# Single node: exact AR(1) per mode (pins phi_k, phi_k^g, the ghost filter)
+
+
+@pytest.mark.parametrize("scheme,tau", [(1, 0.8), (1, 0.55), (1, 2.0), (0, 0.8), (2, 0.8)])
+def test_single_node_mode_statistics(oracle_mod, scheme, tau):
+    """On a 1x1x1 periodic box streaming is the identity and u = 0, so every
+    non-conserved mode is m' = lambda_k m + phi_k r.  Its stationary variance
+    must be the equilibrium value rho0 kT b_k / c_s^2 for every tau, and its
+    lag-1 autocorrelation lambda_k = 1-omega for k = 4..9 and for BGK ghosts,
+    0 for GMF / Reg ghosts (unit relaxation, filtered)."""
+    T = oracle_mod.tables()
+    E, b = T["E"], T["b"]
+    kT, rho0 = 1e-4, 1.0
+    nsteps = 60000
+    box = oracle_mod.Box(1, 1, 1, tau=tau, kT=kT, rho0=rho0, seed=42, scheme=scheme)
+    traj = box.trajectory_node0(nsteps + 200)[200:]
+    m = traj @ E.T                                  # (steps, 27) mode amplitudes
+    # conserved modes stay put (roundoff random walk over 6e4 steps only)
+    assert np.abs(m[:, 0] - rho0).max() < 1e-10
+    assert np.abs(m[:, 1:4]).max() < 1e-10
+    lam_h = 1 - 1 / tau
+    for k in range(4, 27):
+        x = m[:, k] - m[:, k].mean()
+        var = x.var()
+        lag1 = (x[1:] * x[:-1]).mean() / var
+        lam = lam_h if (k <= 9 or scheme == 0) else 0.0
+        # AR(1) estimator spreads
+        neff = nsteps * (1 - lam * lam) / (1 + lam * lam)
+        sd_var = np.sqrt(2.0 / neff)
+        sd_lag = np.sqrt((1 - lam * lam) / nsteps) + 1e-3
+        theory = rho0 * kT * b[k] / CS2
+        assert abs(var / theory - 1) < 5 * sd_var, (k, var / theory)
+        assert abs(lag1 - lam) < 5 * sd_lag, (k, lag1, lam)
+
+
+# --------------------------------------------------------------------------
+# Special cases
+
+
+def test_tau_one_gmf_equals_bgk(oracle_mod):
+    """At tau = 1, lambda = 0 and omega(2-omega) = 1 for every mode, so GMF-FLBM
+    and BGK-FLBM are the same update: identical trajectories for one seed."""
+    T = oracle_mod.tables()
+    w = T["w"]
+    f0 = w[:, None, None, None] * (1 + 0.01 * inputs.population_perturbation(4, 5, 3, 1))
+    out = []
+    for scheme in (0, 1):
+        box = oracle_mod.Box(4, 5, 3, tau=1.0, kT=1e-4, seed=9, scheme=scheme)
+        box.set_f(f0)
+        box.step(30)
+        out.append(box.get_f())
+    assert np.abs(out[0] - out[1]).max() < 1e-15
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_kT0_tau1_collision_is_feq(oracle_mod, scheme):
+    T = oracle_mod.tables()
+    c, w = T["c"].astype(float), T["w"]
+    f = w * (1 + 0.05 * inputs.normal_field(27, seed=4))
+    rho = f.sum()
+    u = c.T @ f / rho
+    fs = oracle_mod.collide_node(scheme, 1.0, 0.0, f)
+    assert np.abs(fs - oracle_mod.feq2(rho, u)).max() < 1e-16
+
+
+def test_reg_full_order_equilibrium_is_product_form(oracle_mod):
+    """Reg-FLBM at tau=1, kT=0 maps f to its full-order equilibrium; that must
+    be the product-form D3Q27 equilibrium
+    rho prod_a w1(c_a)(1 + c_a u_a/c_s^2 + (c_a^2 - c_s^2) u_a^2 / (2 c_s^4))."""
+    T = oracle_mod.tables()
+    c, w = T["c"].astype(float), T["w"]
+    f = w * (1 + 0.2 * inputs.normal_field(27, seed=5))
+    rho = f.sum()
+    u = c.T @ f / rho
+    fs = oracle_mod.collide_node(2, 1.0, 0.0, f)
+    w1 = np.where(c == 0, 2.0 / 3.0, 1.0 / 6.0)
+    fac = w1 * (1 + c * u / CS2 + (c * c - CS2) * u * u / (2 * CS2 * CS2))
+    assert np.abs(fs - rho * fac.prod(1)).max() < 1e-16
+
+
+def _rotate_state(f, c, perm, signs):
+    """Apply the cube symmetry x'_a = signs[a] * x_{perm[a]} to a population
+    field f[i, z, y, x] on a cubic periodic box."""
+    n = f.shape[1]
+    cn = c[:, perm] * signs
+    idx = {tuple(v): i for i, v in enumerate(c)}
+    out = np.empty_like(f)
+    grid = np.indices((n, n, n))[::-1]          # x, y, z coordinates
+    src = [grid[perm[a]] for a in range(3)]
+    dst = [(signs[a] * src[a]) % n for a in range(3)]
+    for i in range(27):
+        j = idx[tuple(cn[i])]
+        out[j][dst[2], dst[1], dst[0]] = f[i][grid[2], grid[1], grid[0]]
+    return out
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+@pytest.mark.parametrize("perm,signs", [((1, 0, 2), (1, 1, 1)), ((1, 0, 2), (-1, 1, 1)),
+                                        ((2, 0, 1), (1, -1, 1)), ((0, 1, 2), (1, 1, -1))])
+def test_kT0_cube_symmetry_covariance(oracle_mod, scheme, perm, signs):
+    """With kT = 0 the update commutes with every symmetry of the cube: a
+    transposed index or wrong sign anywhere in f^eq, a2neq or the Reg
+    equilibrium breaks this."""
+    T = oracle_mod.tables()
+    c, w = T["c"], T["w"]
+    n = 5
+    f0 = w[:, None, None, None] * (1 + 0.05 * inputs.population_perturbation(n, n, n, 21))
+    perm, signs = np.array(perm), np.array(signs)
+    a = oracle_mod.Box(n, n, n, tau=0.7, kT=0.0, scheme=scheme)
+    a.set_f(f0)
+    a.step(6)
+    b = oracle_mod.Box(n, n, n, tau=0.7, kT=0.0, scheme=scheme)
+    b.set_f(_rotate_state(f0, c, perm, signs))
+    b.step(6)
+    assert np.abs(_rotate_state(a.get_f(), c, perm, signs) - b.get_f()).max() < 1e-15
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+def test_center_of_mass_moves_with_total_momentum(oracle_mod, scheme):
+    """Push streaming f_i(x + c_i, t+1) = f*_i(x, t) with a momentum-conserving
+    collision moves the mass centre by exactly the total momentum each step:
+    sum_x x rho(t) - sum_x x rho(0) = t P_x (no wrap while the pulse stays
+    away from the box edges).  A reversed streaming direction gives -t P_x."""
+    nx = 64
+    x = np.arange(nx)
+    ux = 0.05 * np.exp(-((x - nx / 2) / 3.0) ** 2)
+    f0 = np.zeros((27, 1, 1, nx))
+    for i in range(nx):
+        f0[:, 0, 0, i] = oracle_mod.feq2(1.0, [ux[i], 0.01 * ux[i], 0.0])
+    box = oracle_mod.Box(nx, 1, 1, tau=0.8, kT=0.0, seed=3, scheme=scheme)
+    box.set_f(f0)
+    rho0, j0, _ = box.moments()
+    P = j0[0].sum()
+    box.step(15)
+    rho, _, _ = box.moments()
+    shift = (x * rho[0, 0]).sum() - (x * rho0[0, 0]).sum()
+    assert abs(shift - 15 * P) < 1e-9 * abs(P) * 15 + 1e-12, (shift, 15 * P)
+
+
+# --------------------------------------------------------------------------
+# Hydrodynamics: shear-wave viscosity nu = c_s^2 (tau - 1/2)
+
+
+def shear_wave_nu(oracle_mod, scheme, tau, ny):
+    """Decay rate of a noise-off shear wave u_x = A sin(2 pi y / ny), fitted
+    as nu_fit = -ln(a1/a0) / (k^2 (t1 - t0)) after the initial transient."""
+    k = 2 * np.pi / ny
+    nu = CS2 * (tau - 0.5)
+    ux = inputs.sine_profile(ny, 1e-3)
+    f0 = np.zeros((27, 1, ny, 1))
+    for y in range(ny):
+        f0[:, 0, y, 0] = oracle_mod.feq2(1.0, [ux[y], 0.0, 0.0])
+    box = oracle_mod.Box(1, ny, 1, tau=tau, kT=0.0, scheme=scheme)
+    box.set_f(f0)
+    sin = np.sin(k * np.arange(ny))
+    t0 = 20
+    t1 = int(min(4000, 1.5 / (nu * k * k)))
+    box.step(t0)
+    a0 = (box.moments()[1][0, 0, :, 0] * sin).sum()
+    box.step(t1 - t0)
+    a1 = (box.moments()[1][0, 0, :, 0] * sin).sum()
+    return -np.log(a1 / a0) / ((t1 - t0) * k * k)
+
+
+@pytest.mark.parametrize("scheme", [1, 0, 2])
+@pytest.mark.parametrize("tau", [0.55, 1.0, 2.0, 5.0])
+def test_shear_wave_viscosity(oracle_mod, scheme, tau):
+    """nu = c_s^2 (tau - 1/2) (Sec. II).  The lattice decay rate carries an
+    O(k^2) dispersion correction (1.3 % at tau = 5 on ny = 128), so the
+    hydrodynamic limit is taken by Richardson extrapolation over ny = 128,
+    256 (k^2 ratio 4) and must match within 1 %; the raw ny = 128 fit must be
+    within 2 %."""
+    nu = CS2 * (tau - 0.5)
+    n128 = shear_wave_nu(oracle_mod, scheme, tau, 128)
+    n256 = shear_wave_nu(oracle_mod, scheme, tau, 256)
+    nu0 = (4 * n256 - n128) / 3
+    assert abs(n128 / nu - 1) < 0.02, (n128, nu)
+    assert abs(nu0 / nu - 1) < 0.01, (nu0, nu)
+
+
+# --------------------------------------------------------------------------
+# Structure factor
+
+
+def _numpy_shells(m, nshell):
+    nz, ny, nx = m.shape
+    F = np.fft.fftn(m - m.mean())
+    P = np.abs(F) ** 2 / m.size
+    n = [np.fft.fftfreq(L, 1.0 / L) for L in (nz, ny, nx)]
+    for a, L in enumerate((nz, ny, nx)):
+        n[a] = np.where(n[a] == L // 2, -(L // 2), n[a]) if L % 2 == 0 else n[a]
+    NZ, NY, NX = np.meshgrid(*n, indexing="ij")
+    r = np.rint(np.sqrt(NX ** 2 + NY ** 2 + NZ ** 2)).astype(int)
+    S = np.zeros(nshell)
+    cnt = np.zeros(nshell, np.int64)
+    for s in range(1, nshell):
+        sel = r == s
+        cnt[s] = sel.sum()
+        S[s] = P[sel].mean() if cnt[s] else 0.0
+    return S, cnt
+
+
+@pytest.mark.parametrize("shape", [(4, 5, 6), (8, 8, 8), (3, 7, 2)])
+def test_structure_factor_matches_numpy_fft(oracle_mod, shape):
+    m = inputs.normal_field(shape, seed=sum(shape))
+    nshell = 12
+    S, cnt = oracle_mod.structure_factor(m, nshell)
+    S2, cnt2 = _numpy_shells(m, nshell)
+    assert np.array_equal(cnt, cnt2)
+    assert np.allclose(S, S2, rtol=1e-12, atol=1e-14)
+    # Parseval: shells cover every n != 0 when nshell is large enough
+    assert abs((S * cnt).sum() - ((m - m.mean()) ** 2).sum()) < 1e-10
+
+
+def test_structure_factor_plane_wave(oracle_mod):
+    """m = cos(2 pi 3 x / L): |dm(+-3,0,0)|^2 = N/4 and nothing else, so shell 3
+    holds 2 (N/4) spread over its brute-force-counted population."""
+    n = 12
+    x = np.arange(n)
+    m = np.cos(2 * np.pi * 3 * x / n)[None, None, :] * np.ones((n, n, n))
+    S, cnt = oracle_mod.structure_factor(m, 12)
+    rng = range(-n // 2, n // 2)
+    pop = sum(1 for a in rng for b in rng for c in rng
+              if (a or b or c) and round((a * a + b * b + c * c) ** 0.5) == 3)
+    assert cnt[3] == pop
+    assert abs(S[3] - 2 * (n ** 3 / 4) / pop) < 1e-9
+    assert np.abs(np.delete(S, 3)).max() < 1e-20
+
+
+# --------------------------------------------------------------------------
+# Thermal statistics on a small box
+
+
+@pytest.mark.parametrize("tau", [0.8, 2.0])
+def test_equipartition_small_box(oracle_mod, tau):
+    """GMF-FLBM, started from a sample of the lattice invariant measure
+    <df_i df_j> = (rho0 kT / c_s^2) w_i delta_ij, stays there: <u_a^2> =
+    kT/rho0, and the per-node variances of rho, sum_a j_a, sum_a Pi_aa,
+    sum_{a<b} Pi_ab are 3, 3, 5, 1 times rho0 kT."""
+    T = oracle_mod.tables()
+    w = T["w"]
+    n, kT, rho0 = 8, 1e-4, 1.0
+    sd = np.sqrt(rho0 * kT * w / CS2)[:, None, None, None]
+    f0 = w[:, None, None, None] * rho0 + sd * inputs.population_perturbation(n, n, n, 77)
+    box = oracle_mod.Box(n, n, n, tau=tau, kT=kT, rho0=rho0, seed=5)
+    box.set_f(f0)
+    u2, mv = [], []
+    for s in range(150):
+        box.step(8)
+        rho, j, pi = box.moments()
+        u2.append(((j / rho) ** 2).mean(axis=(1, 2, 3)))
+        obs = [rho, j.sum(0), pi[:3].sum(0), pi[3:].sum(0)]
+        mv.append([o.var() for o in obs])
+    u2 = np.mean(u2, 0) / (kT / rho0)
+    mv = np.mean(mv, 0) / (rho0 * kT * np.array([3, 3, 5, 1]))
+    assert np.all(np.abs(u2 - 1) < 0.04), u2
+    assert np.all(np.abs(mv - 1) < 0.04), mv
