@@ -1,0 +1,424 @@
+#!/usr/bin/env python3
+"""Throughput of the fused GMF-FLBM D3Q27 stream-and-collide step on GB300.
+
+Workload (one "step" = one lattice time step of the whole hot path over the
+box): periodic 512^3 box, FP32 deviation populations in place (AA pattern,
+14.5 GB), GMF-FLBM, rho0 = 1, kT = 1e-5, tau = 0.6, fused FP64 reductions on
+every step.  The box starts from a seeded sample of the lattice invariant
+measure so the reported <u_a^2> is an equilibrium value.
+
+Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (bounded sample of the same workload).
+
+Multi-GPU: the path runs independent replica boxes, one per rank ("replicas
+only", weak scaling); torch.distributed is used for the barrier and the
+max-over-ranks time only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(nx=512, ny=512, nz=512, tau=0.6, kT=1e-5, rho0=1.0, seed=20260101, scheme="gmf")
+BYTES_PER_NODE = 27 * 4 * 2          # FP32 populations: 27 reads + 27 writes per update
+CS2 = 1.0 / 3.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_f32_gmf_traffic.txt")
+KERNEL_SOURCES = ["step_kernel.cuh", "lattice.cuh", "internal.h", "step_f32.cu"]
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=512, help="cube edge (512 = the benchmark workload)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------
+# distributed helpers (replicas only)
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, local, ws
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    """Maximum of a per-rank scalar over all ranks (the job's time is its
+    slowest rank's)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes_per_rank: int, steps: int, max_ms: float, ws: int) -> float:
+    """Whole-job lattice updates per second over all ranks, in MLUPS."""
+    return ws * nodes_per_rank * steps / (max_ms / 1e3) / 1e6
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                   "-lms", "100"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                pw.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "of measured"
+    except Exception:
+        return 6800.0, "of fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2601_03806_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(size: int):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
+    scaled to the box size; None if the kernel changed since the capture."""
+    try:
+        kv = {}
+        for ln in open(TRAFFIC_FILE):
+            if ":" in ln and not ln.startswith("#"):
+                k, v = ln.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_hash") != kernel_source_hash():
+            return None
+        per_node = float(kv["dram_bytes_per_node"])
+        return per_node * size ** 3
+    except Exception:
+        return None
+
+
+def thermal_fill(lat, n, kT, rho0, seed):
+    """Seeded sample of the invariant measure written straight into the
+    torch-owned population buffer (natural form at step 0)."""
+    import torch
+    import oracle
+    w = oracle.tables()["w"]
+    buf = lat._buf.view(torch.float32).view(27, -1)
+    gen = torch.Generator(device=buf.device)
+    gen.manual_seed(seed)
+    for i in range(27):
+        buf[i].normal_(0.0, float((rho0 * kT * w[i] / CS2) ** 0.5), generator=gen)
+    torch.cuda.synchronize()
+
+
+def host_mem_available() -> int:
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable:"):
+                return int(ln.split()[1]) * 1024
+    except Exception:
+        pass
+    return 0
+
+
+def oracle_sample(tau, kT, rho0, seed, budget_s=2.0, n=64):
+    """The FP64 oracle as it stands on this host's cores: a bounded sample
+    (n^3 box from a thermal state, same tau/kT/rho0) stepped until ~budget_s
+    of wall time.  Returns (MLUPS, threads, steps, u2 ratio)."""
+    import numpy as np
+    import oracle
+    from synth import inputs
+    oracle.build()
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    w = oracle.tables()["w"]
+    box = oracle.Box(n, n, n, tau, kT, rho0=rho0, seed=seed)
+    sd = np.sqrt(rho0 * kT * w / CS2)[:, None, None, None]
+    box.set_f(w[:, None, None, None] * rho0 + sd * inputs.population_perturbation(n, n, n, seed))
+    box.step(1)
+    steps, t0 = 0, time.perf_counter()
+    u2 = []
+    while True:
+        box.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s and steps >= 3:
+            break
+    rho, j, _ = box.moments()
+    u2 = ((j / rho) ** 2).mean(axis=(1, 2, 3)) / (kT / rho0)
+    return n ** 3 * steps / el / 1e6, threads, steps, [float(x) for x in u2]
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return 0
+    tau, kT, rho0, seed = WORKLOAD["tau"], WORKLOAD["kT"], WORKLOAD["rho0"], WORKLOAD["seed"]
+    import numpy as np
+    import oracle
+    from synth import inputs
+    oracle.build()
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    n = 64
+    w = oracle.tables()["w"]
+    box = oracle.Box(n, n, n, tau, kT, rho0=rho0, seed=seed)
+    sd = np.sqrt(rho0 * kT * w / CS2)[:, None, None, None]
+    box.set_f(w[:, None, None, None] * rho0 + sd * inputs.population_perturbation(n, n, n, seed))
+    box.step(args.warmup)
+    t0 = time.perf_counter()
+    box.step(args.steps)
+    el = time.perf_counter() - t0
+    v = n ** 3 * args.steps / el / 1e6
+    sample = "%d^3 box of the %d^3 workload's parameters, FP64 two-array oracle, %d threads" % (
+        n, args.size, threads)
+    line = {
+        "impl": "reference", "metric": metric_name(), "value": v, "unit": "MLUPS",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.size, ws),
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def metric_name():
+    return "MLUPS of the fused GMF-FLBM D3Q27 stream-and-collide step (HBM roofline fraction beside it)"
+
+
+def workload_config(size, ws):
+    return {"workload": "GMF-FLBM D3Q27 periodic %d^3, FP32 deviation populations AA in place, "
+                        "rho0=1, kT=1e-5, tau=0.6, FP64 reductions every step" % size,
+            "nx": size, "ny": size, "nz": size, "tau": WORKLOAD["tau"], "kT": WORKLOAD["kT"],
+            "rho0": WORKLOAD["rho0"], "scheme": "gmf", "storage": "fp32 deviations, AA in place",
+            "stats_every": 1, "l2": "inputs larger than L2 (%.1f GB state vs 129 MB L2)"
+            % (27 * 4 * size ** 3 / 1e9),
+            "parallelism": "replicas x%d (one independent box per GPU)" % ws}
+
+
+def run_ours(args, rank, local, ws):
+    import numpy as np
+    import torch
+    from paper_2601_03806_gb300 import build as _b
+    _b.build()
+    from paper_2601_03806_gb300 import flbm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.size
+    N = n ** 3
+    tau, kT, rho0 = WORKLOAD["tau"], WORKLOAD["kT"], WORKLOAD["rho0"]
+    seed = WORKLOAD["seed"] + rank
+    stream = torch.cuda.Stream(device=dev)
+    lat = flbm.Lattice(n, n, n, tau, kT, rho0=rho0, seed=seed, precision=flbm.FLBM_FP32,
+                       stats_every=1, torch_memory=True, stream=stream)
+    thermal_fill(lat, n, kT, rho0, seed)
+    lat.step(args.warmup)
+    lat.stats_reset()
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    gpu_id = ("GPU-" + str(uuid)) if uuid is not None else os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]
+
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(ws)
+    with ClockSampler(gpu_id) as clk:
+        lat.timing_enable(True)
+        start.record(stream)
+        lat.step(args.steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+    kernel_ms, launches = lat.timing_read()
+    lat.timing_enable(False)
+    barrier(ws)
+    el_ms = start.elapsed_time(end)
+    max_ms = max_over_ranks(el_ms, ws, dev)
+    value = job_mlups(N, args.steps, max_ms, ws)
+    st = lat.stats()
+
+    k_ms = kernel_ms / max(launches, 1)
+    peak, peak_src = measured_hbm_peak()
+    achieved = BYTES_PER_NODE * N / (k_ms / 1e3) / 1e9
+    traffic = recorded_traffic(n)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": traffic, "kernel": "flbm::k_step<float,float,GMF,*,stats>",
+                "kernel_ms": k_ms, "algorithmic_bytes_per_launch": BYTES_PER_NODE * N}
+
+    u2_ratio = [x / (kT / rho0) for x in st["u2_avg"]]
+
+    # e2e through the C ABI with pinned host buffers: upload the state, K steps
+    # each followed by a stats read, then one moments snapshot to the host.
+    e2e = None
+    if not args.no_e2e:
+        state_bytes = 27 * 4 * N
+        mom_bytes = 10 * 8 * N
+        with_moments = host_mem_available() > 3 * (state_bytes + mom_bytes)
+        hstate = torch.empty(27 * N, dtype=torch.float32, pin_memory=True)
+        lat.get_state(hstate)
+        if with_moments:
+            hrho = torch.empty(N, dtype=torch.float64, pin_memory=True)
+            hj = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
+            hpi = torch.empty(6 * N, dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        lat.set_state(hstate)
+        lat.set_step(args.warmup)
+        for _ in range(args.steps):
+            lat.step(1)
+            lat.stats()
+        if with_moments:
+            rc = flbm.flbm_moments(lat.handle, hrho.data_ptr(), hj.data_ptr(), hpi.data_ptr())
+            if rc != 0:
+                raise RuntimeError(flbm.flbm_last_error(lat.handle))
+        torch.cuda.synchronize()
+        e_ms = (time.perf_counter() - t0) * 1e3
+        e_max = max_over_ranks(e_ms, ws, dev)
+        import ctypes
+        stats_bytes = ctypes.sizeof(flbm.flbm_stats_t) + 16
+        e2e = {"value": job_mlups(N, args.steps, e_max, ws), "unit": "MLUPS",
+               "h2d_bytes_per_step": state_bytes // args.steps,
+               "d2h_bytes_per_step": (mom_bytes if with_moments else 0) // args.steps + stats_bytes,
+               "what": "flbm_set_state from pinned host + K x (flbm_step(1) + flbm_stats)"
+                       + (" + flbm_moments snapshot to pinned host" if with_moments else "")}
+        del hstate
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, threads, steps, u2o = oracle_sample(tau, kT, rho0, WORKLOAD["seed"])
+        cpu = {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+               "sample": "64^3 box with the workload's tau/kT/rho0 from a thermal state, %d steps, "
+                         "FP64 two-array oracle on %d host threads" % (steps, threads),
+               "u2_ratio": u2o}
+
+    if rank == 0:
+        line = {
+            "metric": metric_name(), "value": value, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(n, ws), "roofline": roofline,
+            "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches) + int(args.steps),
+            "clocks": clk.summary(),
+            "equipartition": {"u2_avg_over_kT_rho0": u2_ratio,
+                              "max_abs_error": max(abs(x - 1) for x in u2_ratio),
+                              "er": st["er"], "samples": st["n_samples"]},
+            "mass_rel_drift": st["mass"] / (N * rho0) - 1.0,
+        }
+        print(json.dumps(line), flush=True)
+    lat.close()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, local, ws = dist_setup()
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, ws)
+        return run_ours(args, rank, local, ws)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+            if dist.is_initialized():
+                dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * flbm.h -- C ABI of the GB300 (sm_103a) ghost-mode filtered fluctuating
+ * lattice Boltzmann library (libflbm.so).
+ *
+ * The library advances a periodic nx*ny*nz D3Q27 box with the fluctuating
+ * lattice Boltzmann update of Lauricella, Montessori, Tiribocchi, Succi,
+ * "Ghost-Mode Filtered Fluctuating Lattice Boltzmann Method" (arXiv
+ * 2601.03806):
+ *   - GMF-FLBM, Eq. flbe2 (Sec. II): second-order f^eq, filtered f^neq
+ *     (Eq. moments2), noise amplitudes phi_k (Eq. fluct_phi, k=4..9) and
+ *     phi_k^g (Eq. fluct_phig, k=10..26);
+ *   - BGK-FLBM, Eq. flbe (Sec. II): single relaxation of all modes;
+ *   - Reg-FLBM (Sec. III): full-order Hermite f^eq, unit ghost relaxation.
+ *
+ * Conventions shared by every call
+ *   - Every call returns an int status (flbm_status); no exception or
+ *     longjmp crosses the ABI.  On failure the context's error string
+ *     (flbm_last_error) says why.
+ *   - Node index n = x + nx*(y + ny*z), x fastest.  Population arrays are
+ *     SoA: f[i*N + n], N = nx*ny*nz, with the velocity order
+ *        i = 0      (0,0,0)
+ *        i = 1..6   +x -x +y -y +z -z
+ *        i = 7..18  (+,+,0) (-,-,0) (+,-,0) (-,+,0)   xy plane
+ *                   (+,0,+) (-,0,-) (+,0,-) (-,0,+)   xz plane
+ *                   (0,+,+) (0,-,-) (0,+,-) (0,-,+)   yz plane
+ *        i = 19..26 (+++) (---) (++-) (--+) (+-+) (-+-) (-++) (+--)
+ *     (Table I groups; the order inside a group is this library's choice).
+ *   - Host arrays are owned by the caller; the library never keeps a host
+ *     pointer past the call.  Device memory is owned by the library unless
+ *     flbm_create_ex is given dev_buf, which then must outlive the context.
+ *   - Calls that return host data are synchronous on the context's stream.
+ *     flbm_step returns after the launched steps completed (it reads the
+ *     instability flag back).
+ *   - Noise: Philox4x32-10 (Salmon et al., SC'11), key = (seed lo, seed hi),
+ *     counter = (node, step lo, block j = 0..5, step hi); word m of block j
+ *     feeds mode k = 4 + 4j + m (mode 27 unused); Box-Muller on consecutive
+ *     word pairs with u = ((w >> 9) + 0.5) 2^-23.  The result therefore does
+ *     not depend on launch shape, and a checkpoint (populations + step +
+ *     seed) resumes bit-exactly.
+ */
+#ifndef FLBM_H
+#define FLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FLBM_ABI_VERSION 1
+
+typedef struct flbm_ctx flbm_ctx; /* opaque, owned by the library */
+
+/* Collision scheme (Sec. III compares all three). */
+enum flbm_scheme { FLBM_BGK = 0, FLBM_GMF = 1, FLBM_REG = 2 };
+
+/* Storage precision of the populations.
+ * FLBM_FP64: deviations g_i = f_i - w_i rho0 in double, FP64 arithmetic.
+ * FLBM_FP32: deviations in float, FP32 arithmetic (FP64 only for the global
+ *            reductions and the S(k) accumulators).
+ * FLBM_FP16: deviations in half, FP32 arithmetic (not built yet:
+ *            FLBM_E_UNSUPPORTED). */
+enum flbm_precision { FLBM_FP64 = 0, FLBM_FP32 = 1, FLBM_FP16 = 2 };
+
+enum flbm_status {
+    FLBM_OK = 0,
+    FLBM_E_INVALID = -1,     /* bad argument (sizes, tau <= 0.5, kT < 0, ...) */
+    FLBM_E_NOMEM = -2,       /* device or host allocation failed / buffer too small */
+    FLBM_E_CUDA = -3,        /* a CUDA runtime / cuFFT call failed */
+    FLBM_E_UNSTABLE = -4,    /* a step met rho <= 0 or a non-finite value */
+    FLBM_E_TIMEOUT = -5,     /* reserved: bounded device wait ran out */
+    FLBM_E_UNSUPPORTED = -6  /* valid request this build does not implement */
+};
+
+/* Observables of the equilibration ratio and of S(k) (Sec. III): the local
+ * density, sum_a rho u_a, sum_a Pi_aa, sum_{a<b} Pi_ab, and the momentum
+ * components. Pi_ab = sum_i f_i c_ia c_ib (full second moment). */
+enum flbm_observable {
+    FLBM_OBS_RHO = 0,
+    FLBM_OBS_JSUM = 1,
+    FLBM_OBS_PI_DIAG = 2,
+    FLBM_OBS_PI_OFFDIAG = 3,
+    FLBM_OBS_JX = 4,
+    FLBM_OBS_JY = 5,
+    FLBM_OBS_JZ = 6
+};
+
+typedef struct flbm_params {
+    int32_t nx, ny, nz;    /* box, each >= 1; N * 27 < 2^40 */
+    int32_t scheme;        /* flbm_scheme */
+    int32_t precision;     /* flbm_precision */
+    int32_t noise_rho0;    /* 0: phi_k uses the local rho(x,t); 1: uses rho0 */
+    int32_t stats_every;   /* fused FP64 reductions every k-th step (0: off) */
+    int32_t reserved;      /* must be 0 */
+    double tau;            /* relaxation time, > 0.5 (omega = 1/tau) */
+    double kT;             /* thermal energy k_B T >= 0 (lattice units) */
+    double rho0;           /* reference density > 0; initial state f_i = w_i rho0 */
+    uint64_t seed;         /* Philox key */
+} flbm_params;
+
+/* Statistics of the fused reductions (row a9).  Sums run over all nodes of
+ * the pre-collision state f(x,t) of the reduced steps. */
+typedef struct flbm_stats_t {
+    int64_t step;          /* t of the most recent reduced step */
+    int64_t n_samples;     /* reduced steps accumulated since flbm_stats_reset */
+    double mass;           /* sum_x rho at that step */
+    double mom[3];         /* sum_x rho u_a */
+    double u2[3];          /* mean_x u_a^2 at that step */
+    double u2_avg[3];      /* time average of u2 since reset */
+    double m_mean[4];      /* time-space mean of (rho - rho0, sum j, sum_a Pi_aa - rho0,
+                              sum_{a<b} Pi_ab) */
+    double m_var[4];       /* their time-space variance */
+    double er[4];          /* equilibration ratios m_var / theory, theory =
+                              (3, 3, 5, 1) rho0 kT (lattice ideal-gas invariant
+                              measure); 0 when kT = 0 */
+} flbm_stats_t;
+
+/* Fill p with defaults for a box: FP32 storage, local-rho noise, stats every
+ * step.  Returns FLBM_E_INVALID on a NULL p. */
+int flbm_params_init(flbm_params *p, int nx, int ny, int nz, double tau, double kT,
+                     double rho0, uint64_t seed, int scheme);
+
+/* Device bytes the population state needs (27 N elements of the storage
+ * type, AA-pattern in place).  0 on invalid parameters. */
+size_t flbm_state_bytes(const flbm_params *p);
+
+/* Create a context with flbm_params_init defaults: FP32 deviations, AA in
+ * place, library-owned memory and stream; state f_i = w_i rho0 at step 0.
+ * out receives the context (NULL on failure). */
+int flbm_create(int nx, int ny, int nz, double tau, double kT, double rho0,
+                uint64_t seed, int scheme, flbm_ctx **out);
+
+/* Create from explicit parameters.  dev_buf: NULL, or a device buffer of at
+ * least flbm_state_bytes(p) bytes, 256-byte aligned, that the caller (e.g.
+ * PyTorch) owns and keeps alive; cuda_stream: NULL for a library-owned
+ * stream, else a cudaStream_t on the current device that all work of this
+ * context is ordered on. */
+int flbm_create_ex(const flbm_params *p, void *dev_buf, size_t dev_bytes,
+                   void *cuda_stream, flbm_ctx **out);
+
+/* Advance n >= 0 steps (Eq. flbe2 / flbe per the scheme; one fused
+ * stream-and-collide kernel per step, reductions on the steps selected by
+ * stats_every).  Returns FLBM_E_UNSTABLE if any step met rho <= 0 or a
+ * non-finite density; the step counter is then the t of the first such
+ * step and the populations hold that step's output (restore a checkpoint). */
+int flbm_step(flbm_ctx *c, int64_t n);
+
+/* Moments of the pre-collision state f(x, t) at the current step t (Eqs.
+ * rho, u): rho[N], j[3N] (planes jx, jy, jz), pi[6N] (planes xx, yy, zz, xy,
+ * xz, yz of Pi_ab = sum_i f_i c_ia c_ib).  Any pointer may be NULL. */
+int flbm_moments(flbm_ctx *c, double *rho, double *j, double *pi);
+
+/* Read the fused-reduction statistics (see flbm_stats_t). */
+int flbm_stats(flbm_ctx *c, flbm_stats_t *out);
+
+/* Restart the time averages (e.g. after a warm-up). */
+int flbm_stats_reset(flbm_ctx *c);
+
+/* Normalised-FFT spectrum of one observable of the current state (Sec. III):
+ * dm(n) = N^-1/2 sum_x (m(x) - mean) exp(-2 pi i n.x / L) with integer
+ * n_a in [-L_a/2, L_a/2); shell s = round(|n|), n = 0 excluded.  S[s] =
+ * shell mean of |dm(n)|^2, count[s] = number of wavevectors, s < nshell
+ * (larger shells dropped).  cuFFT R2C (FP32 storage) or D2Z (FP64), FP64
+ * shell accumulation. */
+int flbm_structure_factor(flbm_ctx *c, int observable, int nshell, double *S,
+                          int64_t *count);
+
+/* Absolute populations f_i(x, t) of the current step, FP64, SoA f[i*N+n]. */
+int flbm_get_populations(flbm_ctx *c, double *f);
+int flbm_set_populations(flbm_ctx *c, const double *f);
+
+/* Absolute populations f_i(x, t) at `count` listed nodes (node indices n in
+ * [0, N)), written as f[k*27 + i] for the k-th listed node: a probe for
+ * large boxes where a full readback is impractical.  FLBM_E_INVALID if a
+ * node index is out of range. */
+int flbm_probe(flbm_ctx *c, const int64_t *nodes, int64_t count, double *f);
+
+/* Raw state: deviations g_i = f_i - w_i rho0 in the storage type (double for
+ * FLBM_FP64, float for FLBM_FP32), SoA natural layout, 27 N elements.
+ * Checkpoint = get_state + flbm_get_step; restore = set_state + set_step. */
+int flbm_get_state(flbm_ctx *c, void *host);
+int flbm_set_state(flbm_ctx *c, const void *host);
+
+/* Device timing of the fused step kernel.  While enabled, each step-kernel
+ * launch is bracketed by two CUDA events recorded on the context stream (the
+ * stream the kernel runs on).  flbm_timing_read waits for the recorded
+ * events, returns the summed kernel time in milliseconds and the number of
+ * timed launches since the last read/enable, and clears both. */
+int flbm_timing_enable(flbm_ctx *c, int enable);
+int flbm_timing_read(flbm_ctx *c, double *kernel_ms, int64_t *launches);
+
+int64_t flbm_get_step(const flbm_ctx *c);       /* -1 on NULL */
+int flbm_set_step(flbm_ctx *c, int64_t step);   /* step >= 0 */
+
+/* Parameters the context was created with (copy). */
+int flbm_get_params(const flbm_ctx *c, flbm_params *out);
+
+/* Error text of the last failing call on c (context-owned, valid until the
+ * next call on c); c == NULL gives the thread's last create-time error. */
+const char *flbm_last_error(const flbm_ctx *c);
+
+/* Release everything the context owns (not a caller dev_buf/stream). */
+void flbm_destroy(flbm_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLBM_H */

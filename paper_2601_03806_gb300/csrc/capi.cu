@@ -1,0 +1,623 @@
+// capi.cu -- the extern "C" boundary declared in include/flbm.h.
+//
+// Host-side orchestration only: argument checks, device buffers, the AA
+// parity bookkeeping, the per-step launch sequence and chunked host<->device
+// transfers.  All arithmetic of the method runs in the kernels of
+// step_kernel.cuh and aux.cu; S(k) uses cuFFT for the transform.
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/flbm.h"
+#include "internal.h"
+#include "lattice.cuh"
+
+using namespace flbm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevFlags {
+    unsigned int flag;
+    unsigned int pad;
+    unsigned long long bad_step;
+};
+
+constexpr uint64_t kStageNodes = 1ull << 18;   // nodes per host-transfer chunk
+
+}  // namespace
+
+struct flbm_ctx {
+    flbm_params p{};
+    int device = 0;
+    int nsm = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *g = nullptr;
+    bool own_g = false;
+    size_t g_bytes = 0;
+    uint64_t n = 0;
+    int64_t step = 0;
+    int phase = 0;                 // storage is natural when ((step + phase) & 1) == 0
+    int grid = 1;                  // persistent grid of the step kernel
+    double *partials = nullptr;    // [grid][NSTAT]
+    DevStats *dstats = nullptr;
+    DevFlags *dflags = nullptr;
+    double *stage = nullptr;       // host-transfer staging, kStageNodes * 27 doubles
+    // S(k)
+    cufftHandle plan = 0;
+    bool has_plan = false;
+    void *fft_in = nullptr;
+    void *fft_out = nullptr;
+    double *shell_s = nullptr;
+    unsigned long long *shell_c = nullptr;
+    int shell_cap = 0;
+    // step-kernel timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;   // pairs (start, stop), reused
+    size_t ev_used = 0;            // pairs recorded since the last read
+    std::string err;
+};
+
+namespace {
+
+int fail(flbm_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+#define CK(ctx, call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(ctx, FLBM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKFFT(ctx, call)                                                                  \
+    do {                                                                                  \
+        cufftResult r_ = (call);                                                          \
+        if (r_ != CUFFT_SUCCESS)                                                          \
+            return fail(ctx, FLBM_E_CUDA, std::string(#call) + ": cufft error " + std::to_string(int(r_))); \
+    } while (0)
+
+size_t elem_size(int prec) { return prec == FLBM_FP64 ? 8 : prec == FLBM_FP32 ? 4 : 2; }
+
+int prec_code(const flbm_ctx *c) { return c->p.precision == FLBM_FP64 ? 0 : 1; }
+
+int parity(const flbm_ctx *c) { return int((c->step + c->phase) & 1); }
+
+BoxDesc box_of(const flbm_ctx *c)
+{
+    BoxDesc b;
+    b.nx = uint32_t(c->p.nx);
+    b.ny = uint32_t(c->p.ny);
+    b.nz = uint32_t(c->p.nz);
+    b.n = c->n;
+    b.rho0 = c->p.rho0;
+    b.parity = parity(c);
+    return b;
+}
+
+std::string validate(const flbm_params *p)
+{
+    if (!p) return "params is NULL";
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "nx, ny, nz must be >= 1";
+    const double n = double(p->nx) * double(p->ny) * double(p->nz);
+    if (n * 27.0 >= 1099511627776.0) return "box too large (27 N must be < 2^40)";
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return "tau must be finite and > 0.5";
+    if (!(p->kT >= 0.0) || !std::isfinite(p->kT)) return "kT must be finite and >= 0";
+    if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) return "rho0 must be finite and > 0";
+    if (p->scheme < FLBM_BGK || p->scheme > FLBM_REG) return "unknown scheme";
+    if (p->precision < FLBM_FP64 || p->precision > FLBM_FP16) return "unknown precision";
+    if (p->stats_every < 0) return "stats_every must be >= 0";
+    if (p->noise_rho0 != 0 && p->noise_rho0 != 1) return "noise_rho0 must be 0 or 1";
+    if (p->reserved != 0) return "reserved must be 0";
+    return "";
+}
+
+// phi_k / (b_k sqrt(rho)) of Eqs. fluct_phi (k = 4..9; all k for BGK-FLBM)
+// and fluct_phig (k = 10..26, GMF-FLBM and Reg-FLBM); c_s^2 = 1/3.
+void noise_coefficients(const flbm_params &p, double nc[kQ])
+{
+    const double omega = 1.0 / p.tau;
+    for (int k = 0; k < kQ; ++k) nc[k] = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int c = 0; c < 3; ++c) {
+                const int k = mode_of(a, b, c);
+                if (k < 4) continue;
+                const double bk = b_of(a, b, c);
+                const bool ghost = k >= 10;
+                const double fac = (ghost && p.scheme != FLBM_BGK) ? 1.0 : omega * (2.0 - omega);
+                nc[k] = std::sqrt(p.kT * fac * bk * 3.0) / bk;
+            }
+}
+
+template <typename R>
+StepArgs<R> make_args(const flbm_ctx *c, int64_t t)
+{
+    StepArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    a.nx = uint32_t(c->p.nx);
+    a.ny = uint32_t(c->p.ny);
+    a.nz = uint32_t(c->p.nz);
+    a.cpr = uint32_t((c->p.nx + kBlock - 1) / kBlock);
+    a.n = c->n;
+    a.nchunks = uint64_t(a.cpr) * a.ny * a.nz;
+    a.step = uint64_t(t);
+    a.key0 = uint32_t(c->p.seed & 0xffffffffu);
+    a.key1 = uint32_t(c->p.seed >> 32);
+    a.noise_rho0 = c->p.noise_rho0;
+    a.lambda = R(1.0 - 1.0 / c->p.tau);
+    a.rho0 = R(c->p.rho0);
+    a.sqrt_rho0 = R(std::sqrt(c->p.rho0));
+    double nc[kQ];
+    noise_coefficients(c->p, nc);
+    for (int k = 0; k < kQ; ++k) a.nc[k] = R(nc[k]);
+    a.partials = c->partials;
+    a.flag = &c->dflags->flag;
+    a.bad_step = &c->dflags->bad_step;
+    return a;
+}
+
+int reset_flags(flbm_ctx *c)
+{
+    DevFlags h{0u, 0u, ~0ull};
+    CK(c, cudaMemcpyAsync(c->dflags, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+    return FLBM_OK;
+}
+
+int ensure_stage(flbm_ctx *c)
+{
+    if (c->stage) return FLBM_OK;
+    CK(c, cudaMalloc(&c->stage, kStageNodes * kQ * sizeof(double)));
+    return FLBM_OK;
+}
+
+void release(flbm_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->has_plan) cufftDestroy(c->plan);
+    cudaFree(c->fft_in);
+    cudaFree(c->fft_out);
+    cudaFree(c->shell_s);
+    cudaFree(c->shell_c);
+    cudaFree(c->stage);
+    cudaFree(c->partials);
+    cudaFree(c->dstats);
+    cudaFree(c->dflags);
+    if (c->own_g) cudaFree(c->g);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int create_impl(const flbm_params *p, void *dev_buf, size_t dev_bytes, void *stream, flbm_ctx **out)
+{
+    if (!out) return fail(nullptr, FLBM_E_INVALID, "out is NULL");
+    *out = nullptr;
+    const std::string why = validate(p);
+    if (!why.empty()) return fail(nullptr, FLBM_E_INVALID, why);
+    if (p->precision == FLBM_FP16)
+        return fail(nullptr, FLBM_E_UNSUPPORTED, "FP16 storage is not built in this library");
+    flbm_ctx *c = new (std::nothrow) flbm_ctx;
+    if (!c) return fail(nullptr, FLBM_E_NOMEM, "host allocation failed");
+    c->p = *p;
+    c->n = uint64_t(p->nx) * uint64_t(p->ny) * uint64_t(p->nz);
+    c->g_bytes = c->n * kQ * elem_size(p->precision);
+    int rc = FLBM_OK;
+    auto bail = [&](int code) {
+        g_create_error = c->err;
+        release(c);
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        c->err = std::string("no usable CUDA device: ") + cudaGetErrorString(e);
+        return bail(FLBM_E_CUDA);
+    }
+    if (stream) {
+        c->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return bail(FLBM_E_CUDA); }
+        c->own_stream = true;
+    }
+    if (dev_buf) {
+        if (dev_bytes < c->g_bytes) {
+            c->err = "dev_buf smaller than flbm_state_bytes()";
+            return bail(FLBM_E_NOMEM);
+        }
+        if (reinterpret_cast<uintptr_t>(dev_buf) % 256 != 0) {
+            c->err = "dev_buf must be 256-byte aligned";
+            return bail(FLBM_E_INVALID);
+        }
+        c->g = dev_buf;
+    } else {
+        e = cudaMalloc(&c->g, c->g_bytes);
+        if (e != cudaSuccess) {
+            c->err = std::string("cudaMalloc(populations): ") + cudaGetErrorString(e);
+            return bail(FLBM_E_NOMEM);
+        }
+        c->own_g = true;
+    }
+    // persistent grid: resident CTAs of the reducing kernel (the larger one)
+    const int occ = p->precision == FLBM_FP64 ? step_occupancy_f64(p->scheme, true)
+                                              : step_occupancy_f32(p->scheme, true);
+    const uint64_t nchunks = uint64_t((p->nx + kBlock - 1) / kBlock) * p->ny * p->nz;
+    c->grid = int(std::min<uint64_t>(nchunks, uint64_t(c->nsm) * occ));
+    if (c->grid < 1) c->grid = 1;
+    e = cudaMalloc(&c->partials, size_t(c->grid) * NSTAT * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->dstats, sizeof(DevStats));
+    if (e == cudaSuccess) e = cudaMalloc(&c->dflags, sizeof(DevFlags));
+    if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return bail(FLBM_E_NOMEM); }
+    e = cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->stream);
+    if (e == cudaSuccess) e = launch_fill_rest(c->g, prec_code(c), c->n * kQ, c->stream);
+    if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return bail(FLBM_E_CUDA); }
+    rc = reset_flags(c);
+    if (rc != FLBM_OK) return bail(rc);
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return bail(FLBM_E_CUDA); }
+    *out = c;
+    return FLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int flbm_params_init(flbm_params *p, int nx, int ny, int nz, double tau, double kT, double rho0,
+                     uint64_t seed, int scheme)
+{
+    if (!p) return fail(nullptr, FLBM_E_INVALID, "params is NULL");
+    std::memset(p, 0, sizeof(*p));
+    p->nx = nx;
+    p->ny = ny;
+    p->nz = nz;
+    p->scheme = scheme;
+    p->precision = FLBM_FP32;
+    p->noise_rho0 = 0;
+    p->stats_every = 1;
+    p->tau = tau;
+    p->kT = kT;
+    p->rho0 = rho0;
+    p->seed = seed;
+    return FLBM_OK;
+}
+
+size_t flbm_state_bytes(const flbm_params *p)
+{
+    if (!validate(p).empty()) return 0;
+    return uint64_t(p->nx) * uint64_t(p->ny) * uint64_t(p->nz) * kQ * elem_size(p->precision);
+}
+
+int flbm_create(int nx, int ny, int nz, double tau, double kT, double rho0, uint64_t seed,
+                int scheme, flbm_ctx **out)
+{
+    flbm_params p;
+    flbm_params_init(&p, nx, ny, nz, tau, kT, rho0, seed, scheme);
+    return create_impl(&p, nullptr, 0, nullptr, out);
+}
+
+int flbm_create_ex(const flbm_params *p, void *dev_buf, size_t dev_bytes, void *cuda_stream,
+                   flbm_ctx **out)
+{
+    return create_impl(p, dev_buf, dev_bytes, cuda_stream, out);
+}
+
+int flbm_step(flbm_ctx *c, int64_t n)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (n < 0) return fail(c, FLBM_E_INVALID, "n must be >= 0");
+    const int every = c->p.stats_every;
+    for (int64_t s = 0; s < n; ++s) {
+        const int64_t t = c->step + s;
+        const bool odd = ((t + c->phase) & 1) != 0;
+        const bool stats = every > 0 && (t % every) == 0;
+        cudaError_t e;
+        if (c->timing) {
+            if (c->ev.size() < 2 * (c->ev_used + 1)) {
+                for (int k = 0; k < 2; ++k) {
+                    cudaEvent_t ev;
+                    CK(c, cudaEventCreate(&ev));
+                    c->ev.push_back(ev);
+                }
+            }
+            CK(c, cudaEventRecord(c->ev[2 * c->ev_used], c->stream));
+        }
+        if (c->p.precision == FLBM_FP64)
+            e = launch_step_f64(static_cast<double *>(c->g), make_args<double>(c, t), c->p.scheme, odd,
+                                stats, c->grid, c->stream);
+        else
+            e = launch_step_f32(static_cast<float *>(c->g), make_args<float>(c, t), c->p.scheme, odd,
+                                stats, c->grid, c->stream);
+        if (e != cudaSuccess) return fail(c, FLBM_E_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
+        if (c->timing) {
+            CK(c, cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream));
+            ++c->ev_used;
+        }
+        if (stats) {
+            e = launch_stats_finalize(c->partials, c->grid, c->dstats, t, double(c->n), c->stream);
+            if (e != cudaSuccess) return fail(c, FLBM_E_CUDA, std::string("stats launch: ") + cudaGetErrorString(e));
+        }
+    }
+    c->step += n;
+    DevFlags h;
+    CK(c, cudaMemcpyAsync(&h, c->dflags, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (h.flag) {
+        c->step = int64_t(h.bad_step);
+        return fail(c, FLBM_E_UNSTABLE, "instability: rho <= 0 or non-finite at step " +
+                                            std::to_string(int64_t(h.bad_step)));
+    }
+    return FLBM_OK;
+}
+
+int flbm_moments(flbm_ctx *c, double *rho, double *j, double *pi)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    int rc = ensure_stage(c);
+    if (rc) return rc;
+    const BoxDesc b = box_of(c);
+    const uint64_t N = c->n;
+    for (uint64_t n0 = 0; n0 < N; n0 += kStageNodes) {
+        const uint64_t cn = std::min<uint64_t>(kStageNodes, N - n0);
+        CK(c, launch_moments(c->g, prec_code(c), b, n0, cn, c->stage, c->stream));
+        const size_t w = cn * sizeof(double);
+        if (rho) CK(c, cudaMemcpyAsync(rho + n0, c->stage, w, cudaMemcpyDeviceToHost, c->stream));
+        if (j) CK(c, cudaMemcpy2DAsync(j + n0, N * sizeof(double), c->stage + cn, w, w, 3,
+                                       cudaMemcpyDeviceToHost, c->stream));
+        if (pi) CK(c, cudaMemcpy2DAsync(pi + n0, N * sizeof(double), c->stage + 4 * cn, w, w, 6,
+                                        cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLBM_OK;
+}
+
+int flbm_stats(flbm_ctx *c, flbm_stats_t *out)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (!out) return fail(c, FLBM_E_INVALID, "out is NULL");
+    DevStats h;
+    CK(c, cudaMemcpyAsync(&h, c->dstats, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    std::memset(out, 0, sizeof(*out));
+    const double N = double(c->n);
+    out->step = h.nsamp ? h.step : -1;
+    out->n_samples = h.nsamp;
+    out->mass = N * c->p.rho0 + h.last[S_DRHO];
+    for (int a = 0; a < 3; ++a) {
+        out->mom[a] = h.last[S_JX + a];
+        out->u2[a] = h.last[S_UX2 + a] / N;
+        out->u2_avg[a] = h.nsamp ? h.acc_u2[a] / double(h.nsamp) : 0.0;
+    }
+    const double th[4] = {3.0, 3.0, 5.0, 1.0};
+    for (int k = 0; k < 4; ++k) {
+        if (!h.nsamp) continue;
+        const double m = h.acc_m[k] / double(h.nsamp);
+        const double m2 = h.acc_m2[k] / double(h.nsamp);
+        out->m_mean[k] = m;
+        out->m_var[k] = m2 - m * m;
+        const double t = th[k] * c->p.rho0 * c->p.kT;
+        out->er[k] = t > 0 ? out->m_var[k] / t : 0.0;
+    }
+    return FLBM_OK;
+}
+
+int flbm_stats_reset(flbm_ctx *c)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    CK(c, cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLBM_OK;
+}
+
+int flbm_structure_factor(flbm_ctx *c, int observable, int nshell, double *S, int64_t *count)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (observable < FLBM_OBS_RHO || observable > FLBM_OBS_JZ) return fail(c, FLBM_E_INVALID, "unknown observable");
+    if (nshell < 1 || nshell > 3072) return fail(c, FLBM_E_INVALID, "nshell must be in [1, 3072]");
+    if (!S || !count) return fail(c, FLBM_E_INVALID, "S and count must not be NULL");
+    const bool dbl = c->p.precision == FLBM_FP64;
+    const size_t rs = dbl ? sizeof(double) : sizeof(float);
+    const uint64_t nspec = uint64_t(c->p.nx / 2 + 1) * c->p.ny * c->p.nz;
+    if (!c->has_plan) {
+        CK(c, cudaMalloc(&c->fft_in, c->n * rs));
+        CK(c, cudaMalloc(&c->fft_out, nspec * 2 * rs));
+        CKFFT(c, cufftPlan3d(&c->plan, c->p.nz, c->p.ny, c->p.nx, dbl ? CUFFT_D2Z : CUFFT_R2C));
+        c->has_plan = true;
+    }
+    CKFFT(c, cufftSetStream(c->plan, c->stream));
+    if (nshell > c->shell_cap) {
+        cudaFree(c->shell_s);
+        cudaFree(c->shell_c);
+        c->shell_s = nullptr;
+        c->shell_c = nullptr;
+        c->shell_cap = 0;
+        CK(c, cudaMalloc(&c->shell_s, nshell * sizeof(double)));
+        CK(c, cudaMalloc(&c->shell_c, nshell * sizeof(unsigned long long)));
+        c->shell_cap = nshell;
+    }
+    const BoxDesc b = box_of(c);
+    CK(c, launch_observable(c->g, prec_code(c), b, observable, c->fft_in, c->stream));
+    if (dbl)
+        CKFFT(c, cufftExecD2Z(c->plan, static_cast<cufftDoubleReal *>(c->fft_in),
+                              static_cast<cufftDoubleComplex *>(c->fft_out)));
+    else
+        CKFFT(c, cufftExecR2C(c->plan, static_cast<cufftReal *>(c->fft_in),
+                              static_cast<cufftComplex *>(c->fft_out)));
+    CK(c, cudaMemsetAsync(c->shell_s, 0, nshell * sizeof(double), c->stream));
+    CK(c, cudaMemsetAsync(c->shell_c, 0, nshell * sizeof(unsigned long long), c->stream));
+    CK(c, launch_shells(c->fft_out, prec_code(c), b, nshell, c->shell_s, c->shell_c, c->stream));
+    CK(c, cudaMemcpyAsync(S, c->shell_s, nshell * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(count, c->shell_c, nshell * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int s = 0; s < nshell; ++s)
+        if (count[s] > 0) S[s] /= double(count[s]);
+    return FLBM_OK;
+}
+
+int flbm_get_populations(flbm_ctx *c, double *f)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (!f) return fail(c, FLBM_E_INVALID, "f is NULL");
+    int rc = ensure_stage(c);
+    if (rc) return rc;
+    const BoxDesc b = box_of(c);
+    const uint64_t N = c->n;
+    for (uint64_t n0 = 0; n0 < N; n0 += kStageNodes) {
+        const uint64_t cn = std::min<uint64_t>(kStageNodes, N - n0);
+        CK(c, launch_gather_f(c->g, prec_code(c), b, n0, cn, c->stage, false, c->stream));
+        const size_t w = cn * sizeof(double);
+        CK(c, cudaMemcpy2DAsync(f + n0, N * sizeof(double), c->stage, w, w, kQ,
+                                cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLBM_OK;
+}
+
+int flbm_set_populations(flbm_ctx *c, const double *f)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (!f) return fail(c, FLBM_E_INVALID, "f is NULL");
+    int rc = ensure_stage(c);
+    if (rc) return rc;
+    BoxDesc b = box_of(c);
+    b.parity = 0;
+    const uint64_t N = c->n;
+    for (uint64_t n0 = 0; n0 < N; n0 += kStageNodes) {
+        const uint64_t cn = std::min<uint64_t>(kStageNodes, N - n0);
+        const size_t w = cn * sizeof(double);
+        CK(c, cudaMemcpy2DAsync(c->stage, w, f + n0, N * sizeof(double), w, kQ,
+                                cudaMemcpyHostToDevice, c->stream));
+        CK(c, launch_scatter_f(c->g, prec_code(c), b, n0, cn, c->stage, c->stream));
+    }
+    c->phase = int(c->step & 1);   // natural form at the current step
+    rc = reset_flags(c);
+    if (rc) return rc;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLBM_OK;
+}
+
+int flbm_probe(flbm_ctx *c, const int64_t *nodes, int64_t count, double *f)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (count < 0 || (count > 0 && (!nodes || !f))) return fail(c, FLBM_E_INVALID, "bad probe arguments");
+    for (int64_t k = 0; k < count; ++k)
+        if (nodes[k] < 0 || uint64_t(nodes[k]) >= c->n)
+            return fail(c, FLBM_E_INVALID, "probe node index out of range");
+    int rc = ensure_stage(c);
+    if (rc) return rc;
+    const BoxDesc b = box_of(c);
+    // staging holds kStageNodes*27 doubles: node list + 27 outputs per node
+    const int64_t chunk = int64_t(kStageNodes * kQ / (kQ + 1));
+    long long *dn = reinterpret_cast<long long *>(c->stage);
+    for (int64_t k0 = 0; k0 < count; k0 += chunk) {
+        const int64_t cn = std::min<int64_t>(chunk, count - k0);
+        double *dout = c->stage + chunk;
+        CK(c, cudaMemcpyAsync(dn, nodes + k0, cn * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+        CK(c, launch_probe(c->g, prec_code(c), b, dn, cn, dout, c->stream));
+        CK(c, cudaMemcpyAsync(f + k0 * kQ, dout, cn * kQ * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLBM_OK;
+}
+
+int flbm_get_state(flbm_ctx *c, void *host)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (!host) return fail(c, FLBM_E_INVALID, "host is NULL");
+    const size_t es = elem_size(c->p.precision);
+    if (parity(c) == 0) {
+        CK(c, cudaMemcpyAsync(host, c->g, c->g_bytes, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        int rc = ensure_stage(c);
+        if (rc) return rc;
+        const BoxDesc b = box_of(c);
+        const uint64_t N = c->n;
+        for (uint64_t n0 = 0; n0 < N; n0 += kStageNodes) {
+            const uint64_t cn = std::min<uint64_t>(kStageNodes, N - n0);
+            CK(c, launch_gather_state(c->g, prec_code(c), b, n0, cn, c->stage, c->stream));
+            CK(c, cudaMemcpy2DAsync(static_cast<char *>(host) + n0 * es, N * es, c->stage, cn * es,
+                                    cn * es, kQ, cudaMemcpyDeviceToHost, c->stream));
+        }
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLBM_OK;
+}
+
+int flbm_set_state(flbm_ctx *c, const void *host)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (!host) return fail(c, FLBM_E_INVALID, "host is NULL");
+    CK(c, cudaMemcpyAsync(c->g, host, c->g_bytes, cudaMemcpyHostToDevice, c->stream));
+    c->phase = int(c->step & 1);
+    int rc = reset_flags(c);
+    if (rc) return rc;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLBM_OK;
+}
+
+int flbm_timing_enable(flbm_ctx *c, int enable)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    c->timing = enable != 0;
+    c->ev_used = 0;
+    return FLBM_OK;
+}
+
+int flbm_timing_read(flbm_ctx *c, double *kernel_ms, int64_t *launches)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (!kernel_ms || !launches) return fail(c, FLBM_E_INVALID, "NULL output");
+    double tot = 0.0;
+    for (size_t k = 0; k < c->ev_used; ++k) {
+        CK(c, cudaEventSynchronize(c->ev[2 * k + 1]));
+        float ms = 0.f;
+        CK(c, cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]));
+        tot += ms;
+    }
+    *kernel_ms = tot;
+    *launches = int64_t(c->ev_used);
+    c->ev_used = 0;
+    return FLBM_OK;
+}
+
+int64_t flbm_get_step(const flbm_ctx *c) { return c ? c->step : -1; }
+
+int flbm_set_step(flbm_ctx *c, int64_t step)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (step < 0) return fail(c, FLBM_E_INVALID, "step must be >= 0");
+    const int par = parity(c);
+    c->step = step;
+    c->phase = int((par - (step & 1)) & 1);
+    return FLBM_OK;
+}
+
+int flbm_get_params(const flbm_ctx *c, flbm_params *out)
+{
+    if (!c || !out) return fail(nullptr, FLBM_E_INVALID, "NULL argument");
+    *out = c->p;
+    return FLBM_OK;
+}
+
+const char *flbm_last_error(const flbm_ctx *c)
+{
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+void flbm_destroy(flbm_ctx *c) { release(c); }
+
+}  // extern "C"

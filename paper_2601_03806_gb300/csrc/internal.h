@@ -1,0 +1,83 @@
+// internal.h -- structures shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace flbm {
+
+constexpr int kQ = 27;
+constexpr int NSTAT = 14;     // fused reduction slots, see StatSlot
+constexpr int kBlock = 128;   // threads per CTA of the step kernel (one x-row chunk)
+
+// Slots of the fused FP64 reductions (row a9).  Sums over nodes of the
+// pre-collision state: drho = rho - rho0, j, u^2 and the four
+// equilibration-ratio observables m1..m4 (Sec. III) and their squares.
+enum StatSlot {
+    S_DRHO = 0, S_JX, S_JY, S_JZ, S_UX2, S_UY2, S_UZ2,
+    S_M2, S_M3, S_M4, S_M1SQ, S_M2SQ, S_M3SQ, S_M4SQ
+};
+
+template <typename R>
+struct StepArgs {
+    uint32_t nx, ny, nz, cpr;     // box; x-chunks of kBlock nodes per row
+    uint64_t n;                   // nodes
+    uint64_t nchunks;             // cpr * ny * nz
+    uint64_t step;                // t of this collision (noise counter)
+    uint32_t key0, key1;          // Philox key = seed
+    int32_t noise_rho0;           // phi_k uses rho0 instead of rho(x,t)
+    int32_t pad_;
+    R lambda;                     // 1 - omega
+    R rho0;
+    R sqrt_rho0;
+    R nc[kQ];                     // phi_k / (b_k sqrt(rho)), k >= 4 (0 below)
+    double *partials;             // [gridDim.x][NSTAT] when reducing
+    unsigned int *flag;           // instability flag
+    unsigned long long *bad_step; // first step that met rho <= 0 / non-finite
+};
+
+// Device-side accumulators of the fused reductions.
+struct DevStats {
+    double last[NSTAT];    // global sums of the most recent reduced step
+    double acc_u2[3];      // sum over reduced steps of mean_x u_a^2
+    double acc_m[4];       // sum over reduced steps of mean_x m_k
+    double acc_m2[4];      // sum over reduced steps of mean_x m_k^2
+    long long step;        // t of the most recent reduced step
+    long long nsamp;       // reduced steps since reset
+};
+
+// Step-kernel launchers (step_f64.cu, step_f32.cu).
+cudaError_t launch_step_f64(double *g, const StepArgs<double> &a, int scheme, bool odd,
+                            bool stats, int grid, cudaStream_t s);
+cudaError_t launch_step_f32(float *g, const StepArgs<float> &a, int scheme, bool odd,
+                            bool stats, int grid, cudaStream_t s);
+// Resident CTAs per SM of the step kernel for (precision, scheme, stats).
+int step_occupancy_f64(int scheme, bool stats);
+int step_occupancy_f32(int scheme, bool stats);
+
+// Auxiliary kernels (aux.cu).  `prec` is 0 (double storage) or 1 (float).
+struct BoxDesc {
+    uint32_t nx, ny, nz;
+    uint64_t n;
+    double rho0;
+    int parity;            // 0: storage natural; 1: AA-shifted (odd form)
+};
+cudaError_t launch_fill_rest(void *g, int prec, uint64_t count, cudaStream_t s);
+cudaError_t launch_gather_f(const void *g, int prec, const BoxDesc &b, uint64_t n0, uint64_t cn,
+                            double *out, bool deviations, cudaStream_t s);
+cudaError_t launch_gather_state(const void *g, int prec, const BoxDesc &b, uint64_t n0,
+                                uint64_t cn, void *out, cudaStream_t s);
+cudaError_t launch_scatter_f(void *g, int prec, const BoxDesc &b, uint64_t n0, uint64_t cn,
+                             const double *in, cudaStream_t s);
+cudaError_t launch_probe(const void *g, int prec, const BoxDesc &b, const long long *nodes,
+                         long long count, double *out, cudaStream_t s);
+cudaError_t launch_moments(const void *g, int prec, const BoxDesc &b, uint64_t n0, uint64_t cn,
+                           double *out, cudaStream_t s);
+cudaError_t launch_observable(const void *g, int prec, const BoxDesc &b, int obs, void *field,
+                              cudaStream_t s);
+cudaError_t launch_shells(const void *spec, int prec, const BoxDesc &b, int nshell, double *S,
+                          unsigned long long *cnt, cudaStream_t s);
+cudaError_t launch_stats_finalize(const double *partials, int nblocks, DevStats *st,
+                                  long long step, double n, cudaStream_t s);
+
+}  // namespace flbm

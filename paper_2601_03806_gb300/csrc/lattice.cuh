@@ -1,0 +1,155 @@
+// lattice.cuh -- D3Q27 lattice, tensor-product Hermite basis and the
+// counter-based noise source, as compile-time device code.
+//
+// Everything here folds to immediates inside fully unrolled loops; there are
+// no run-time tables.
+//
+// Basis (Table II).  Every Table II vector is a tensor product
+//   e_k(c) = p_a(c_x) p_b(c_y) p_c(c_z),  p_0 = 1, p_1 = c, p_2 = c^2 - c_s^2,
+// with per-axis degrees (a,b,c) read off its Hermite symbol (H_{x^2 y} ->
+// (2,1,0)), and b_k = beta_a beta_b beta_c with beta = (1, 1/3, 2/9); the
+// weights factor as w_i = w1(c_x) w1(c_y) w1(c_z), w1(0) = 2/3, w1(+-1) = 1/6
+// (Table I).  The library therefore evaluates the forward projection and the
+// reconstruction f_i = w_i sum_k e_ki M_k / b_k (Eqs. expeq/expneq) as three
+// 1-D passes over 3-point lines instead of a dense 27x27 product.
+#pragma once
+
+#include <cstdint>
+
+namespace flbm {
+
+constexpr int Q = 27;
+
+// Velocity slot of c = (cx,cy,cz) in the ABI order (Table I groups):
+// rest; +x -x +y -y +z -z; xy, xz, yz planes as (++,--,+-,-+); corners
+// (+++),(---),(++-),(--+),(+-+),(-+-),(-++),(+--).
+__host__ __device__ constexpr int slot_of(int cx, int cy, int cz)
+{
+    const int s = cx * cx + cy * cy + cz * cz;
+    if (s == 0) return 0;
+    if (s == 1) {
+        const int axis = cx ? 0 : (cy ? 1 : 2);
+        const int v = cx + cy + cz;
+        return 1 + 2 * axis + (v < 0 ? 1 : 0);
+    }
+    if (s == 2) {
+        const int plane = (cz == 0) ? 0 : ((cy == 0) ? 1 : 2);
+        const int u = (plane == 2) ? cy : cx;
+        const int v = (plane == 0) ? cy : cz;
+        const int pat = (u > 0 && v > 0) ? 0 : (u < 0 && v < 0) ? 1 : (u > 0) ? 2 : 3;
+        return 7 + 4 * plane + pat;
+    }
+    // corners: a "first" member has at most one negative component; its
+    // opposite follows it.
+    const int neg = (cx < 0) + (cy < 0) + (cz < 0);
+    const bool first = neg <= 1;
+    const int ax = first ? cx : -cx, ay = first ? cy : -cy, az = first ? cz : -cz;
+    const int q = (ax > 0 && ay > 0 && az > 0) ? 0 : (az < 0) ? 1 : (ay < 0) ? 2 : 3;
+    return 19 + 2 * q + (first ? 0 : 1);
+}
+
+// 1-D weights and Hermite polynomial values (c in {-1,0,1}, d in {0,1,2}).
+__host__ __device__ constexpr double w1(int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+__host__ __device__ constexpr double p1d(int d, int c)
+{
+    return d == 0 ? 1.0 : (d == 1 ? double(c) : double(c * c) - 1.0 / 3.0);
+}
+__host__ __device__ constexpr double beta1d(int d)
+{
+    return d == 0 ? 1.0 : (d == 1 ? 1.0 / 3.0 : 2.0 / 9.0);
+}
+
+// Table II mode index k of the tensor-product degrees (a,b,c).
+__host__ __device__ constexpr int mode_of(int a, int b, int c)
+{
+    // listing order of Table II
+    return (a == 0 && b == 0 && c == 0) ? 0 :
+           (a == 1 && b == 0 && c == 0) ? 1 :
+           (a == 0 && b == 1 && c == 0) ? 2 :
+           (a == 0 && b == 0 && c == 1) ? 3 :
+           (a == 2 && b == 0 && c == 0) ? 4 :
+           (a == 0 && b == 2 && c == 0) ? 5 :
+           (a == 0 && b == 0 && c == 2) ? 6 :
+           (a == 1 && b == 1 && c == 0) ? 7 :
+           (a == 1 && b == 0 && c == 1) ? 8 :
+           (a == 0 && b == 1 && c == 1) ? 9 :
+           (a == 2 && b == 1 && c == 0) ? 10 :   // x^2 y
+           (a == 2 && b == 0 && c == 1) ? 11 :   // x^2 z
+           (a == 1 && b == 2 && c == 0) ? 12 :   // y^2 x
+           (a == 1 && b == 0 && c == 2) ? 13 :   // z^2 x
+           (a == 0 && b == 2 && c == 1) ? 14 :   // y^2 z
+           (a == 0 && b == 1 && c == 2) ? 15 :   // z^2 y
+           (a == 1 && b == 1 && c == 1) ? 16 :   // xyz
+           (a == 2 && b == 2 && c == 0) ? 17 :   // x^2 y^2
+           (a == 2 && b == 0 && c == 2) ? 18 :   // x^2 z^2
+           (a == 0 && b == 2 && c == 2) ? 19 :   // y^2 z^2
+           (a == 1 && b == 1 && c == 2) ? 20 :   // x y z^2
+           (a == 1 && b == 2 && c == 1) ? 21 :   // x z y^2
+           (a == 2 && b == 1 && c == 1) ? 22 :   // y z x^2
+           (a == 2 && b == 1 && c == 2) ? 23 :   // x^2 y z^2
+           (a == 2 && b == 2 && c == 1) ? 24 :   // x^2 z y^2
+           (a == 1 && b == 2 && c == 2) ? 25 :   // y^2 x z^2
+                                          26;    // x^2 y^2 z^2
+}
+
+__host__ __device__ constexpr int mode_order(int a, int b, int c) { return a + b + c; }
+__host__ __device__ constexpr double b_of(int a, int b, int c)
+{
+    return beta1d(a) * beta1d(b) * beta1d(c);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 block function (Salmon, Moraes, Dror, Shaw, SC'11): ten
+// rounds of two 32x32->64 multiplies with a Weyl-sequence key schedule.
+struct u32x4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint64_t p0 = uint64_t(0xD2511F53u) * c.x;
+        const uint64_t p1 = uint64_t(0xCD9E8D57u) * c.z;
+        c = u32x4{uint32_t(p1 >> 32) ^ c.y ^ k0, uint32_t(p1),
+                  uint32_t(p0 >> 32) ^ c.w ^ k1, uint32_t(p0)};
+    }
+    return c;
+}
+
+// 23-bit uniform in (0,1): ((w >> 9) + 0.5) 2^-23, exact in float and double.
+__device__ __forceinline__ float uniform23f(uint32_t w)
+{
+    return __fmaf_rn(__uint2float_rn(w >> 9), 0x1p-23f, 0x1p-24f);
+}
+__device__ __forceinline__ double uniform23d(uint32_t w)
+{
+    return __fma_rn(double(w >> 9), 0x1p-23, 0x1p-24);
+}
+
+// Box-Muller (1958): (r_a, r_b) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
+// FP32: accurate logf; the angle is taken as 2 pi (u2 - 1/2) in (-pi, pi),
+// where the hardware sin/cos approximations hold their absolute error bound,
+// and the half-turn is undone by a sign flip.
+__device__ __forceinline__ void box_muller(uint32_t w1u, uint32_t w2u, float &ra, float &rb)
+{
+    const float u1 = uniform23f(w1u);
+    const float u2 = uniform23f(w2u);
+    const float t = -2.0f * logf(u1);
+    const float rad = t * rsqrtf(t);
+    float s, c;
+    __sincosf(6.2831853071795865f * (u2 - 0.5f), &s, &c);
+    ra = -rad * c;
+    rb = -rad * s;
+}
+__device__ __forceinline__ void box_muller(uint32_t w1u, uint32_t w2u, double &ra, double &rb)
+{
+    const double u1 = uniform23d(w1u);
+    const double u2 = uniform23d(w2u);
+    const double rad = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    ra = rad * c;
+    rb = rad * s;
+}
+
+}  // namespace flbm

@@ -1,0 +1,265 @@
+"""Thin ctypes binding of libflbm.so (include/flbm.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch is optional plumbing: ``Lattice(..., torch_memory=True)``
+lets torch own the population buffer and the CUDA stream.
+
+If the shared library is missing this module raises at import time; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libflbm.so")
+
+FLBM_BGK, FLBM_GMF, FLBM_REG = 0, 1, 2
+FLBM_FP64, FLBM_FP32, FLBM_FP16 = 0, 1, 2
+FLBM_OK, FLBM_E_INVALID, FLBM_E_NOMEM, FLBM_E_CUDA = 0, -1, -2, -3
+FLBM_E_UNSTABLE, FLBM_E_TIMEOUT, FLBM_E_UNSUPPORTED = -4, -5, -6
+(FLBM_OBS_RHO, FLBM_OBS_JSUM, FLBM_OBS_PI_DIAG, FLBM_OBS_PI_OFFDIAG,
+ FLBM_OBS_JX, FLBM_OBS_JY, FLBM_OBS_JZ) = range(7)
+SCHEMES = {"bgk": FLBM_BGK, "gmf": FLBM_GMF, "reg": FLBM_REG}
+PRECISIONS = {"fp64": FLBM_FP64, "fp32": FLBM_FP32, "fp16": FLBM_FP16}
+Q = 27
+
+
+class flbm_params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("scheme", C.c_int32), ("precision", C.c_int32),
+                ("noise_rho0", C.c_int32), ("stats_every", C.c_int32),
+                ("reserved", C.c_int32), ("tau", C.c_double), ("kT", C.c_double),
+                ("rho0", C.c_double), ("seed", C.c_uint64)]
+
+
+class flbm_stats_t(C.Structure):
+    _fields_ = [("step", C.c_int64), ("n_samples", C.c_int64), ("mass", C.c_double),
+                ("mom", C.c_double * 3), ("u2", C.c_double * 3), ("u2_avg", C.c_double * 3),
+                ("m_mean", C.c_double * 4), ("m_var", C.c_double * 4), ("er", C.c_double * 4)]
+
+    def as_dict(self):
+        return {"step": self.step, "n_samples": self.n_samples, "mass": self.mass,
+                "mom": list(self.mom), "u2": list(self.u2), "u2_avg": list(self.u2_avg),
+                "m_mean": list(self.m_mean), "m_var": list(self.m_var), "er": list(self.er)}
+
+
+class FlbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("flbm error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libflbm.so is not built (run __graft_entry__.build() or "
+                          "python paper_2601_03806_gb300/build.py); there is no CPU fallback")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, u64, d = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double
+    P = C.POINTER
+    sig = {
+        "flbm_params_init": ([P(flbm_params), i32, i32, i32, d, d, d, u64, i32], i32),
+        "flbm_state_bytes": ([P(flbm_params)], C.c_size_t),
+        "flbm_create": ([i32, i32, i32, d, d, d, u64, i32, P(vp)], i32),
+        "flbm_create_ex": ([P(flbm_params), vp, C.c_size_t, vp, P(vp)], i32),
+        "flbm_step": ([vp, i64], i32),
+        "flbm_moments": ([vp, vp, vp, vp], i32),
+        "flbm_stats": ([vp, P(flbm_stats_t)], i32),
+        "flbm_stats_reset": ([vp], i32),
+        "flbm_structure_factor": ([vp, i32, i32, vp, vp], i32),
+        "flbm_get_populations": ([vp, vp], i32),
+        "flbm_set_populations": ([vp, vp], i32),
+        "flbm_probe": ([vp, vp, i64, vp], i32),
+        "flbm_get_state": ([vp, vp], i32),
+        "flbm_set_state": ([vp, vp], i32),
+        "flbm_timing_enable": ([vp, i32], i32),
+        "flbm_timing_read": ([vp, vp, vp], i32),
+        "flbm_get_step": ([vp], i64),
+        "flbm_set_step": ([vp, i64], i32),
+        "flbm_get_params": ([vp, P(flbm_params)], i32),
+        "flbm_last_error": ([vp], C.c_char_p),
+        "flbm_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
+
+
+lib = _load()
+
+# Same-name module-level functions (raw C ABI).
+flbm_params_init = lib.flbm_params_init
+flbm_state_bytes = lib.flbm_state_bytes
+flbm_create = lib.flbm_create
+flbm_create_ex = lib.flbm_create_ex
+flbm_step = lib.flbm_step
+flbm_moments = lib.flbm_moments
+flbm_stats = lib.flbm_stats
+flbm_stats_reset = lib.flbm_stats_reset
+flbm_structure_factor = lib.flbm_structure_factor
+flbm_get_populations = lib.flbm_get_populations
+flbm_set_populations = lib.flbm_set_populations
+flbm_probe = lib.flbm_probe
+flbm_get_state = lib.flbm_get_state
+flbm_set_state = lib.flbm_set_state
+flbm_timing_enable = lib.flbm_timing_enable
+flbm_timing_read = lib.flbm_timing_read
+flbm_get_step = lib.flbm_get_step
+flbm_set_step = lib.flbm_set_step
+flbm_get_params = lib.flbm_get_params
+flbm_last_error = lib.flbm_last_error
+flbm_destroy = lib.flbm_destroy
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def make_params(nx, ny, nz, tau, kT, rho0=1.0, seed=0, scheme=FLBM_GMF, precision=FLBM_FP32,
+                noise_rho0=False, stats_every=1) -> flbm_params:
+    p = flbm_params()
+    lib.flbm_params_init(C.byref(p), nx, ny, nz, tau, kT, rho0, seed,
+                         SCHEMES.get(scheme, scheme) if isinstance(scheme, str) else scheme)
+    p.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+    p.noise_rho0 = int(bool(noise_rho0))
+    p.stats_every = int(stats_every)
+    return p
+
+
+class Lattice:
+    """Owning wrapper of one flbm_ctx.
+
+    torch_memory=True: the population buffer is a torch CUDA tensor and the
+    work is ordered on torch's current stream (``self.stream``)."""
+
+    def __init__(self, nx, ny, nz, tau, kT, rho0=1.0, seed=0, scheme=FLBM_GMF,
+                 precision=FLBM_FP32, noise_rho0=False, stats_every=1, torch_memory=False,
+                 stream=None):
+        self.params = make_params(nx, ny, nz, tau, kT, rho0, seed, scheme, precision,
+                                  noise_rho0, stats_every)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.n = nx * ny * nz
+        self._h = C.c_void_p()
+        self._buf = None
+        self.stream = stream
+        dev, nbytes, sp = None, 0, None
+        if torch_memory:
+            import torch
+            nbytes = int(lib.flbm_state_bytes(C.byref(self.params)))
+            if nbytes == 0:
+                raise FlbmError(FLBM_E_INVALID, "invalid parameters")
+            self._buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            dev = self._buf.data_ptr()
+            if self.stream is None:
+                self.stream = torch.cuda.current_stream()
+        if self.stream is not None:
+            sp = self.stream.cuda_stream if hasattr(self.stream, "cuda_stream") else int(self.stream)
+        rc = lib.flbm_create_ex(C.byref(self.params), dev, nbytes, sp, C.byref(self._h))
+        if rc != FLBM_OK:
+            raise FlbmError(rc, lib.flbm_last_error(None).decode())
+
+    def _check(self, rc):
+        if rc != FLBM_OK:
+            raise FlbmError(rc, lib.flbm_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            lib.flbm_destroy(self._h)
+            self._h = C.c_void_p()
+        self._buf = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def step_count(self) -> int:
+        return int(lib.flbm_get_step(self._h))
+
+    def set_step(self, t: int) -> None:
+        self._check(lib.flbm_set_step(self._h, int(t)))
+
+    def step(self, n: int = 1) -> None:
+        self._check(lib.flbm_step(self._h, int(n)))
+
+    def timing_enable(self, on: bool = True) -> None:
+        self._check(lib.flbm_timing_enable(self._h, int(bool(on))))
+
+    def timing_read(self):
+        """(summed step-kernel milliseconds, launches) since the last read."""
+        ms = C.c_double()
+        cnt = C.c_int64()
+        self._check(lib.flbm_timing_read(self._h, C.byref(ms), C.byref(cnt)))
+        return ms.value, cnt.value
+
+    def moments(self):
+        shape = (self.nz, self.ny, self.nx)
+        rho = np.empty(shape)
+        j = np.empty((3,) + shape)
+        pi = np.empty((6,) + shape)
+        self._check(lib.flbm_moments(self._h, _ptr(rho), _ptr(j), _ptr(pi)))
+        return rho, j, pi
+
+    def stats(self) -> dict:
+        s = flbm_stats_t()
+        self._check(lib.flbm_stats(self._h, C.byref(s)))
+        return s.as_dict()
+
+    def stats_reset(self) -> None:
+        self._check(lib.flbm_stats_reset(self._h))
+
+    def structure_factor(self, observable: int, nshell: int):
+        S = np.zeros(nshell)
+        cnt = np.zeros(nshell, np.int64)
+        self._check(lib.flbm_structure_factor(self._h, int(observable), int(nshell), _ptr(S), _ptr(cnt)))
+        return S, cnt
+
+    def get_populations(self) -> np.ndarray:
+        f = np.empty((Q, self.nz, self.ny, self.nx))
+        self._check(lib.flbm_get_populations(self._h, _ptr(f)))
+        return f
+
+    def set_populations(self, f) -> None:
+        ff = np.ascontiguousarray(f, np.float64).reshape(Q, self.nz, self.ny, self.nx)
+        self._check(lib.flbm_set_populations(self._h, _ptr(ff)))
+
+    def probe(self, nodes) -> np.ndarray:
+        """Absolute f_i at the listed node indices, shape (len(nodes), 27)."""
+        nn = np.ascontiguousarray(nodes, np.int64)
+        out = np.empty((nn.size, Q))
+        self._check(lib.flbm_probe(self._h, _ptr(nn), nn.size, _ptr(out)))
+        return out
+
+    def state_dtype(self):
+        return np.float64 if self.params.precision == FLBM_FP64 else np.float32
+
+    def get_state(self, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty((Q, self.nz, self.ny, self.nx), self.state_dtype())
+        self._check(lib.flbm_get_state(self._h, _ptr(out) if isinstance(out, np.ndarray)
+                                       else C.c_void_p(out.data_ptr())))
+        return out
+
+    def set_state(self, g) -> None:
+        if isinstance(g, np.ndarray):
+            gg = np.ascontiguousarray(g, self.state_dtype())
+            self._check(lib.flbm_set_state(self._h, _ptr(gg)))
+        else:  # a pinned torch tensor
+            self._check(lib.flbm_set_state(self._h, C.c_void_p(g.data_ptr())))

@@ -1,0 +1,92 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+include/flbm.h declares, the ctypes structures match the C layout, and
+argument validation rejects bad input before touching the device."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "flbm.h")
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_2601_03806_gb300 import build
+    build.build()
+    from paper_2601_03806_gb300 import flbm
+    return flbm
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(flbm_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(F):
+    names = declared_functions()
+    assert len(names) >= 19
+    out = subprocess.run(["nm", "-D", "--defined-only", F.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(flbm_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(F, n), n          # same-name binding
+
+
+def test_struct_layout_matches_header(F, tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "flbm.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(flbm_params), offsetof(flbm_params, tau),
+         offsetof(flbm_params, seed), sizeof(flbm_stats_t), offsetof(flbm_stats_t, er));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+    assert vals == [C.sizeof(F.flbm_params), F.flbm_params.tau.offset, F.flbm_params.seed.offset,
+                    C.sizeof(F.flbm_stats_t), F.flbm_stats_t.er.offset]
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(tau=0.5), -1), (dict(tau=0.3), -1), (dict(kT=-1e-5), -1), (dict(rho0=0.0), -1),
+    (dict(nx=0), -1), (dict(scheme=7), -1), (dict(precision=2), -6), (dict(stats_every=-1), -1),
+    (dict(tau=float("nan")), -1),
+])
+def test_validation_before_device(F, kw, code):
+    args = dict(nx=8, ny=8, nz=8, tau=0.8, kT=1e-5, rho0=1.0, seed=1, scheme=1, precision=1,
+                stats_every=1)
+    args.update(kw)
+    p = F.make_params(args["nx"], args["ny"], args["nz"], args["tau"], args["kT"], args["rho0"],
+                      args["seed"], args["scheme"], args["precision"], False, args["stats_every"])
+    h = C.c_void_p()
+    rc = F.flbm_create_ex(C.byref(p), None, 0, None, C.byref(h))
+    assert rc == code
+    assert not h.value
+    assert F.flbm_last_error(None)
+
+
+def test_state_bytes_and_params(F):
+    p = F.make_params(512, 512, 512, 0.6, 1e-5)
+    assert F.flbm_state_bytes(C.byref(p)) == 27 * 512 ** 3 * 4
+    p = F.make_params(16, 16, 16, 0.8, 1e-4, precision=F.FLBM_FP64)
+    assert F.flbm_state_bytes(C.byref(p)) == 27 * 16 ** 3 * 8
+    p.tau = 0.4
+    assert F.flbm_state_bytes(C.byref(p)) == 0
+
+
+def test_null_context_calls_are_rejected(F):
+    assert F.flbm_step(None, 1) == F.FLBM_E_INVALID
+    assert F.flbm_get_step(None) == -1
+    assert F.flbm_stats_reset(None) == F.FLBM_E_INVALID
+    F.flbm_destroy(None)
