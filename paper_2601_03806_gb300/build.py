@@ -19,6 +19,9 @@ SOURCES = ["capi.cu", "aux.cu", "step_f32.cu", "step_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I" + os.path.join(ROOT, "include")]
+# extra nvcc flags, e.g. FLBM_NVCC_FLAGS="-DFLBM_MIN_BLOCKS=5" (register bound
+# of the step kernel); the default build uses none
+EXTRA = os.environ.get("FLBM_NVCC_FLAGS", "").split()
 
 
 def _nvcc() -> str:
@@ -29,6 +32,9 @@ def _nvcc() -> str:
 
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    stamp = os.path.join(BUILD, "flags")
+    if os.path.exists(stamp) and open(stamp).read() != " ".join(EXTRA):
+        return float("inf")
     files.append(os.path.join(ROOT, "include", "flbm.h"))
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)
@@ -42,7 +48,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *EXTRA, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
@@ -58,6 +64,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
     os.replace(tmp, OUT)
+    with open(os.path.join(BUILD, "flags"), "w") as fh:
+        fh.write(" ".join(EXTRA))
     return OUT
 
 

@@ -270,7 +270,7 @@ __global__ void k_stats_finalize(const double *partials, int nblocks, DevStats *
         for (int s = 0; s < NSTAT; ++s) st->last[s] = red[s][0];
         for (int a = 0; a < 3; ++a) st->acc_u2[a] += red[S_UX2 + a][0] / n;
         st->acc_m[0] += red[S_DRHO][0] / n;
-        st->acc_m[1] += red[S_M2][0] / n;
+        st->acc_m[1] += (red[S_JX][0] + red[S_JY][0] + red[S_JZ][0]) / n;
         st->acc_m[2] += red[S_M3][0] / n;
         st->acc_m[3] += red[S_M4][0] / n;
         for (int k = 0; k < 4; ++k) st->acc_m2[k] += red[S_M1SQ + k][0] / n;

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -46,8 +47,9 @@ struct flbm_ctx {
     uint64_t n = 0;
     int64_t step = 0;
     int phase = 0;                 // storage is natural when ((step + phase) & 1) == 0
-    int grid = 1;                  // persistent grid of the step kernel
-    double *partials = nullptr;    // [grid][NSTAT]
+    int grid = 1;                  // persistent grid of the direct step kernel
+    int row_grid = 0;              // persistent grid of the TMA row pipeline (0: unused)
+    double *partials = nullptr;    // [max(grid, row_grid)][NSTAT]
     DevStats *dstats = nullptr;
     DevFlags *dflags = nullptr;
     double *stage = nullptr;       // host-transfer staging, kStageNodes * 27 doubles
@@ -124,21 +126,41 @@ std::string validate(const flbm_params *p)
     return "";
 }
 
-// phi_k / (b_k sqrt(rho)) of Eqs. fluct_phi (k = 4..9; all k for BGK-FLBM)
-// and fluct_phig (k = 10..26, GMF-FLBM and Reg-FLBM); c_s^2 = 1/3.
-void noise_coefficients(const flbm_params &p, double nc[kQ])
+// phi_k / sqrt(rho) of Eqs. fluct_phi (k = 4..9; all k for BGK-FLBM) and
+// fluct_phig (k = 10..26, GMF-FLBM and Reg-FLBM); c_s^2 = 1/3.
+double noise_amplitude(const flbm_params &p, int k, double bk)
 {
     const double omega = 1.0 / p.tau;
-    for (int k = 0; k < kQ; ++k) nc[k] = 0.0;
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-            for (int c = 0; c < 3; ++c) {
-                const int k = mode_of(a, b, c);
-                if (k < 4) continue;
-                const double bk = b_of(a, b, c);
-                const bool ghost = k >= 10;
-                const double fac = (ghost && p.scheme != FLBM_BGK) ? 1.0 : omega * (2.0 - omega);
-                nc[k] = std::sqrt(p.kT * fac * bk * 3.0) / bk;
+    const bool ghost = k >= 10;
+    const double fac = (ghost && p.scheme != FLBM_BGK) ? 1.0 : omega * (2.0 - omega);
+    return std::sqrt(p.kT * fac * bk * 3.0);
+}
+
+// Mode coefficients of Eq. flbe2 (GMF), Eq. flbe (BGK) and Reg-FLBM in the
+// kernel's scaled units: post-collision M_k = a_eq,k + lambda_k (m_k - a_eq,k)
+// + phi_k r_k, with lambda_k = 1 - omega for k = 4..9 (all non-conserved k
+// for BGK) and 0 for GMF/Reg ghosts; a_eq,k = rho u^deg for Reg ghosts, 0 for
+// BGK ghosts (second-order f^eq), absent for GMF ghosts (filtered).
+template <typename R>
+void mode_coefficients(const flbm_params &p, StepArgs<R> &a)
+{
+    const double omega = 1.0 / p.tau, lam = 1.0 - omega;
+    for (int k = 0; k < kQ; ++k) a.cq_m[k] = a.cq_eq[k] = a.ncq[k] = R(0);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int l = 0; l < 3; ++l) {
+                const int k = mode_of(i, j, l);
+                const int ord = mode_order(i, j, l);
+                if (ord < 2) continue;
+                const double syn = syn_scale(i, j, l), fwd = fwd_scale(i, j, l);
+                double lk, eq;
+                if (ord == 2) { lk = lam; eq = omega; }
+                else if (p.scheme == FLBM_BGK) { lk = lam; eq = 0.0; }
+                else if (p.scheme == FLBM_REG) { lk = 0.0; eq = 1.0; }
+                else { lk = 0.0; eq = 0.0; }
+                a.cq_m[k] = R(syn * lk / fwd);
+                a.cq_eq[k] = R(syn * eq);
+                a.ncq[k] = R(syn * noise_amplitude(p, k, b_of(i, j, l)));
             }
 }
 
@@ -154,15 +176,19 @@ StepArgs<R> make_args(const flbm_ctx *c, int64_t t)
     a.n = c->n;
     a.nchunks = uint64_t(a.cpr) * a.ny * a.nz;
     a.step = uint64_t(t);
-    a.key0 = uint32_t(c->p.seed & 0xffffffffu);
-    a.key1 = uint32_t(c->p.seed >> 32);
+    // Philox4x32-10 key schedule: key = seed, bumped by the Weyl constants
+    // (0x9E3779B9, 0xBB67AE85) before each round after the first
+    uint32_t k0 = uint32_t(c->p.seed & 0xffffffffu), k1 = uint32_t(c->p.seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        a.rk[2 * r] = k0;
+        a.rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
     a.noise_rho0 = c->p.noise_rho0;
-    a.lambda = R(1.0 - 1.0 / c->p.tau);
     a.rho0 = R(c->p.rho0);
     a.sqrt_rho0 = R(std::sqrt(c->p.rho0));
-    double nc[kQ];
-    noise_coefficients(c->p, nc);
-    for (int k = 0; k < kQ; ++k) a.nc[k] = R(nc[k]);
+    mode_coefficients<R>(c->p, a);
     a.partials = c->partials;
     a.flag = &c->dflags->flag;
     a.bad_step = &c->dflags->bad_step;
@@ -252,13 +278,30 @@ int create_impl(const flbm_params *p, void *dev_buf, size_t dev_bytes, void *str
         }
         c->own_g = true;
     }
-    // persistent grid: resident CTAs of the reducing kernel (the larger one)
-    const int occ = p->precision == FLBM_FP64 ? step_occupancy_f64(p->scheme, true)
-                                              : step_occupancy_f32(p->scheme, true);
+    // persistent grids: resident CTAs of the reducing (larger) variants
+    int occ = 1, occ_rows = 0;
+    if (p->precision == FLBM_FP64)
+        step_occupancy_f64(p->scheme, uint32_t(p->nx), true, occ, occ_rows);
+    else
+        step_occupancy_f32(p->scheme, uint32_t(p->nx), c->n, true, occ, occ_rows);
     const uint64_t nchunks = uint64_t((p->nx + kBlock - 1) / kBlock) * p->ny * p->nz;
-    c->grid = int(std::min<uint64_t>(nchunks, uint64_t(c->nsm) * occ));
+    // FLBM_CTAS_PER_SM (environment) caps the direct kernel's grid below the
+    // occupancy limit; a tuning knob, the default is the occupancy limit
+    int per_sm = occ;
+    if (const char *env = std::getenv("FLBM_CTAS_PER_SM")) {
+        const int v = std::atoi(env);
+        if (v > 0 && v < occ) per_sm = v;
+    }
+    c->grid = int(std::min<uint64_t>(nchunks, uint64_t(c->nsm) * per_sm));
     if (c->grid < 1) c->grid = 1;
-    e = cudaMalloc(&c->partials, size_t(c->grid) * NSTAT * sizeof(double));
+    // FLBM_ROWS=0 (environment) disables the TMA row pipeline
+    const char *rows_env = std::getenv("FLBM_ROWS");
+    if (occ_rows > 0 && !(rows_env && std::atoi(rows_env) == 0)) {
+        const uint64_t nrows = uint64_t(p->ny) * p->nz;
+        c->row_grid = int(std::min<uint64_t>(nrows, uint64_t(c->nsm) * occ_rows));
+    }
+    const int max_grid = std::max(c->grid, c->row_grid);
+    e = cudaMalloc(&c->partials, size_t(max_grid) * NSTAT * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->dstats, sizeof(DevStats));
     if (e == cudaSuccess) e = cudaMalloc(&c->dflags, sizeof(DevFlags));
     if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return bail(FLBM_E_NOMEM); }
@@ -338,17 +381,18 @@ int flbm_step(flbm_ctx *c, int64_t n)
         }
         if (c->p.precision == FLBM_FP64)
             e = launch_step_f64(static_cast<double *>(c->g), make_args<double>(c, t), c->p.scheme, odd,
-                                stats, c->grid, c->stream);
+                                stats, c->grid, c->row_grid, c->stream);
         else
             e = launch_step_f32(static_cast<float *>(c->g), make_args<float>(c, t), c->p.scheme, odd,
-                                stats, c->grid, c->stream);
+                                stats, c->grid, c->row_grid, c->stream);
         if (e != cudaSuccess) return fail(c, FLBM_E_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
         if (c->timing) {
             CK(c, cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream));
             ++c->ev_used;
         }
         if (stats) {
-            e = launch_stats_finalize(c->partials, c->grid, c->dstats, t, double(c->n), c->stream);
+            e = launch_stats_finalize(c->partials, c->row_grid > 0 ? c->row_grid : c->grid, c->dstats,
+                                      t, double(c->n), c->stream);
             if (e != cudaSuccess) return fail(c, FLBM_E_CUDA, std::string("stats launch: ") + cudaGetErrorString(e));
         }
     }
@@ -356,6 +400,8 @@ int flbm_step(flbm_ctx *c, int64_t n)
     DevFlags h;
     CK(c, cudaMemcpyAsync(&h, c->dflags, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    if (h.flag & 2u)
+        return fail(c, FLBM_E_TIMEOUT, "a bounded device wait ran out during the last steps");
     if (h.flag) {
         c->step = int64_t(h.bad_step);
         return fail(c, FLBM_E_UNSTABLE, "instability: rho <= 0 or non-finite at step " +

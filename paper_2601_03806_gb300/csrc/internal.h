@@ -7,15 +7,22 @@
 namespace flbm {
 
 constexpr int kQ = 27;
-constexpr int NSTAT = 14;     // fused reduction slots, see StatSlot
+constexpr int NSTAT = 13;     // fused reduction slots, see StatSlot
 constexpr int kBlock = 128;   // threads per CTA of the step kernel (one x-row chunk)
 
+// Minimum resident CTAs per SM requested from the compiler for the step
+// kernel (bounds its registers per thread); a build option.
+#ifndef FLBM_MIN_BLOCKS
+#define FLBM_MIN_BLOCKS 5
+#endif
 // Slots of the fused FP64 reductions (row a9).  Sums over nodes of the
 // pre-collision state: drho = rho - rho0, j, u^2 and the four
-// equilibration-ratio observables m1..m4 (Sec. III) and their squares.
+// equilibration-ratio observables m1 = drho, m2 = sum_a j_a (its sum is
+// S_JX + S_JY + S_JZ), m3 = sum_a Pi_aa - rho0, m4 = sum_{a<b} Pi_ab, and
+// their squares.
 enum StatSlot {
     S_DRHO = 0, S_JX, S_JY, S_JZ, S_UX2, S_UY2, S_UZ2,
-    S_M2, S_M3, S_M4, S_M1SQ, S_M2SQ, S_M3SQ, S_M4SQ
+    S_M3, S_M4, S_M1SQ, S_M2SQ, S_M3SQ, S_M4SQ
 };
 
 template <typename R>
@@ -24,15 +31,21 @@ struct StepArgs {
     uint64_t n;                   // nodes
     uint64_t nchunks;             // cpr * ny * nz
     uint64_t step;                // t of this collision (noise counter)
-    uint32_t key0, key1;          // Philox key = seed
+    uint32_t rk[20];              // Philox round keys (k0, k1) of rounds 0..9
     int32_t noise_rho0;           // phi_k uses rho0 instead of rho(x,t)
     int32_t pad_;
-    R lambda;                     // 1 - omega
     R rho0;
     R sqrt_rho0;
-    R nc[kQ];                     // phi_k / (b_k sqrt(rho)), k >= 4 (0 below)
+    // Per-mode coefficients of the post-collision amplitudes in the
+    // reconstruction's prescaled units (Q_k = syn_scale_k M_k):
+    //   Q_k = cq_m[k] * (fwd_scale_k m_k) + cq_eq[k] * a_eq,k + ncq[k] sqrt(rho) r_k
+    // with m_k the pre-collision Hermite moment, a_eq,k = rho u^deg(k), r_k
+    // the k-th standard normal (k >= 4).
+    R cq_m[kQ];
+    R cq_eq[kQ];
+    R ncq[kQ];
     double *partials;             // [gridDim.x][NSTAT] when reducing
-    unsigned int *flag;           // instability flag
+    unsigned int *flag;           // bit 0: instability; bit 1: a bounded wait ran out
     unsigned long long *bad_step; // first step that met rho <= 0 / non-finite
 };
 
@@ -46,14 +59,17 @@ struct DevStats {
     long long nsamp;       // reduced steps since reset
 };
 
-// Step-kernel launchers (step_f64.cu, step_f32.cu).
+// Step-kernel launchers (step_f64.cu, step_f32.cu).  grid: CTAs of the
+// direct kernel; row_grid: CTAs of the TMA row pipeline (0: do not use it).
 cudaError_t launch_step_f64(double *g, const StepArgs<double> &a, int scheme, bool odd,
-                            bool stats, int grid, cudaStream_t s);
+                            bool stats, int grid, int row_grid, cudaStream_t s);
 cudaError_t launch_step_f32(float *g, const StepArgs<float> &a, int scheme, bool odd,
-                            bool stats, int grid, cudaStream_t s);
-// Resident CTAs per SM of the step kernel for (precision, scheme, stats).
-int step_occupancy_f64(int scheme, bool stats);
-int step_occupancy_f32(int scheme, bool stats);
+                            bool stats, int grid, int row_grid, cudaStream_t s);
+// Resident CTAs per SM of the direct kernel and of the row pipeline (0 when
+// it does not serve rows of length nx) for (precision, scheme, stats); also
+// prepares the kernels' shared-memory attributes on the current device.
+void step_occupancy_f64(int scheme, uint32_t nx, bool stats, int &direct, int &rows);
+void step_occupancy_f32(int scheme, uint32_t nx, uint64_t n, bool stats, int &direct, int &rows);
 
 // Auxiliary kernels (aux.cu).  `prec` is 0 (double storage) or 1 (float).
 struct BoxDesc {

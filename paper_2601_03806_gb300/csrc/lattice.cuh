@@ -92,10 +92,35 @@ __host__ __device__ constexpr int mode_of(int a, int b, int c)
                                           26;    // x^2 y^2 z^2
 }
 
+// Inverse of mode_of: per-axis degrees of Table II mode k, packed a + 3b + 9c.
+__host__ __device__ constexpr int mode_deg(int k)
+{
+    for (int c = 0; c < 3; ++c)
+        for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 3; ++a)
+                if (mode_of(a, b, c) == k) return a + 3 * b + 9 * c;
+    return -1;
+}
+
 __host__ __device__ constexpr int mode_order(int a, int b, int c) { return a + b + c; }
 __host__ __device__ constexpr double b_of(int a, int b, int c)
 {
     return beta1d(a) * beta1d(b) * beta1d(c);
+}
+
+// Scales of the kernel's transforms.  The forward pass returns
+// fwd_scale * M_abc (its degree-2 line sum is 2 s - o = 3 sum v p_2(c)); the
+// reconstruction consumes Q_abc = syn_scale * M_abc with syn_scale =
+// prod kappa(d), kappa = (1/6, 1/2, 1/2) = per-axis w1-prescale / beta, which
+// makes every 1-D synthesis pass (p0 - p1 + p2, 4 p0 - 2 p2, p0 + p1 + p2).
+__host__ __device__ constexpr double fwd_scale(int a, int b, int c)
+{
+    return (a == 2 ? 3.0 : 1.0) * (b == 2 ? 3.0 : 1.0) * (c == 2 ? 3.0 : 1.0);
+}
+__host__ __device__ constexpr double kappa1d(int d) { return d == 0 ? 1.0 / 6.0 : 0.5; }
+__host__ __device__ constexpr double syn_scale(int a, int b, int c)
+{
+    return kappa1d(a) * kappa1d(b) * kappa1d(c);
 }
 
 // ---------------------------------------------------------------------------
@@ -103,53 +128,56 @@ __host__ __device__ constexpr double b_of(int a, int b, int c)
 // rounds of two 32x32->64 multiplies with a Weyl-sequence key schedule.
 struct u32x4 { uint32_t x, y, z, w; };
 
-__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1)
+// rk holds the round keys (k0, k1) of rounds 0..9: the key, bumped by the
+// Weyl constants 0x9E3779B9 / 0xBB67AE85 before every round after the first
+// (precomputed on the host, so the kernel reads them as constants).
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, const uint32_t (&rk)[20])
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
         const uint64_t p0 = uint64_t(0xD2511F53u) * c.x;
         const uint64_t p1 = uint64_t(0xCD9E8D57u) * c.z;
-        c = u32x4{uint32_t(p1 >> 32) ^ c.y ^ k0, uint32_t(p1),
-                  uint32_t(p0 >> 32) ^ c.w ^ k1, uint32_t(p0)};
+        c = u32x4{uint32_t(p1 >> 32) ^ c.y ^ rk[2 * r], uint32_t(p1),
+                  uint32_t(p0 >> 32) ^ c.w ^ rk[2 * r + 1], uint32_t(p0)};
     }
     return c;
 }
 
 // 23-bit uniform in (0,1): ((w >> 9) + 0.5) 2^-23, exact in float and double.
+// FP32 builds it from the bits: (1 + m 2^-23) - (1 - 2^-24) is exact.
 __device__ __forceinline__ float uniform23f(uint32_t w)
 {
-    return __fmaf_rn(__uint2float_rn(w >> 9), 0x1p-23f, 0x1p-24f);
+    return __uint_as_float(0x3f800000u | (w >> 9)) - (1.0f - 0x1p-24f);
 }
 __device__ __forceinline__ double uniform23d(uint32_t w)
 {
     return __fma_rn(double(w >> 9), 0x1p-23, 0x1p-24);
 }
 
-// Box-Muller (1958): (r_a, r_b) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
-// FP32: accurate logf; the angle is taken as 2 pi (u2 - 1/2) in (-pi, pi),
-// where the hardware sin/cos approximations hold their absolute error bound,
-// and the half-turn is undone by a sign flip.
-__device__ __forceinline__ void box_muller(uint32_t w1u, uint32_t w2u, float &ra, float &rb)
+// Box-Muller (1958) in polar form: r_a = rad * ca, r_b = rad * sa with
+// r_a, r_b = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
+// FP32: hardware log2, whose absolute error is <= 2^-22 on [0.5, 1) and
+// <= 2 ulp below 0.5.  The radius then has absolute error <= ln2 2^-22 / rad
+// (~1.7e-7 / rad): below 1e-6 when u1 <= 0.986 (98.6 % of draws) and at most
+// 4.7e-4 at the smallest radius 3.5e-4 (u1 = 1 - 2^-24).  The angle is taken
+// as 2 pi u2 - pi in (-pi, pi), where the hardware sin/cos hold their
+// 2^-21.4 absolute error bound; the half-turn is undone by the sign of rad.
+__device__ __forceinline__ void box_muller(uint32_t w1u, uint32_t w2u, float &rad, float &ca,
+                                           float &sa)
 {
     const float u1 = uniform23f(w1u);
     const float u2 = uniform23f(w2u);
-    const float t = -2.0f * logf(u1);
-    const float rad = t * rsqrtf(t);
-    float s, c;
-    __sincosf(6.2831853071795865f * (u2 - 0.5f), &s, &c);
-    ra = -rad * c;
-    rb = -rad * s;
+    const float t = -1.3862943611198906f * __log2f(u1);   // -2 ln u1
+    rad = -(t * rsqrtf(t));
+    __sincosf(__fmaf_rn(u2, 6.2831853071795865f, -3.1415926535897932f), &sa, &ca);
 }
-__device__ __forceinline__ void box_muller(uint32_t w1u, uint32_t w2u, double &ra, double &rb)
+__device__ __forceinline__ void box_muller(uint32_t w1u, uint32_t w2u, double &rad, double &ca,
+                                           double &sa)
 {
     const double u1 = uniform23d(w1u);
     const double u2 = uniform23d(w2u);
-    const double rad = sqrt(-2.0 * log(u1));
-    double s, c;
-    sincospi(2.0 * u2, &s, &c);
-    ra = rad * c;
-    rb = rad * s;
+    rad = sqrt(-2.0 * log(u1));
+    sincospi(2.0 * u2, &sa, &ca);
 }
 
 }  // namespace flbm

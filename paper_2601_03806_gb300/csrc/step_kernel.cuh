@@ -1,20 +1,15 @@
-// step_kernel.cuh -- fused D3Q27 fluctuating-LB stream-and-collide kernel.
+// step_kernel.cuh -- fused D3Q27 fluctuating-LB stream-and-collide kernels.
 //
-// One thread updates one node per loop iteration; a CTA owns a chunk of
-// kBlock consecutive x of one (y, z) row, so every population plane is read
-// and written as contiguous 4/8-byte-per-lane warp accesses.  The grid is a
-// persistent multiple of the SM count that strides over row chunks.
-//
-// Storage: deviations g_i = f_i - w_i rho0, SoA planes g[i*N + n], updated
-// in place with the AA pattern (no second array):
+// Storage: deviations g_i = f_i - w_i rho0, SoA planes g[i*N + n] (node
+// n = x + nx (y + ny z)), updated in place with the AA pattern:
 //   even form (natural): node x reads f_i from slot i at x and writes the
 //     post-collision f*_i to slot opp(i) at x;
 //   odd form: node x reads f_i from slot opp(i) at x - c_i and writes f*_i to
 //     slot i at x + c_i.
 // Both forms realise f_i(x + c_i, t+1) = f*_i(x, t) (LHS of Eq. flbe2) on a
-// periodic box, and each thread reads exactly the locations it writes.
+// periodic box, and the set of locations a node reads is the set it writes.
 //
-// Per node (Eq. flbe2 in mode space):
+// Per node (Eq. flbe2 in mode space), collide_core:
 //   a2  forward Hermite projection (three 1-D passes): drho, j_a, m_ab
 //   a3  a2neq_ab = m_ab - rho u_a u_b (equal to Eq. moments2 because the
 //       second-order f^eq has second Hermite moment rho u_a u_b)
@@ -24,14 +19,35 @@
 //   a6  M_k += phi_k r_k  (Eqs. fluct_phi / fluct_phig), r_k from
 //       Philox4x32-10 keyed on (seed; node, step, block) + Box-Muller
 //   a7  f*_i = w_i sum_k e_ki M_k / b_k (three 1-D passes), minus w_i rho0
-//   a8  AA store
 //   a9  optional per-thread partial sums for the FP64 reductions
+//
+// Two kernels move the data (a1 load, a8 store):
+//   k_step_rows  (rows whose x-extent is a multiple of 32 and fits shared
+//                memory): a persistent, warp-specialised CTA owns whole
+//                x-rows.  Its producer warp moves, per row, the 27 aligned
+//                plane segments the row reads -- from the 9 neighbouring rows
+//                in the odd form -- into shared memory with TMA bulk copies
+//                (cp.async.bulk, one lane per segment) completing on a "full"
+//                mbarrier, two rows ahead of the compute warps.  The compute
+//                warps apply the periodic +-1 x-shift inside shared memory,
+//                collide, overwrite the same segments (a node's read set is
+//                its write set) and release the stage on an "empty"
+//                mbarrier; the producer then bulk-stores the segments back.
+//                All HBM traffic is aligned bulk transfers and no CTA-wide
+//                barrier sits in the loop.
+//   k_step       (any box): one thread per node, a CTA per 128-node chunk of
+//                a row, direct coalesced loads and stores.
 #pragma once
+
+#include <type_traits>
 
 #include "internal.h"
 #include "lattice.cuh"
 
 namespace flbm {
+
+// ---------------------------------------------------------------------------
+// element access
 
 template <typename S, typename R> struct Conv;
 template <> struct Conv<double, double> {
@@ -39,8 +55,10 @@ template <> struct Conv<double, double> {
     static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
 };
 template <> struct Conv<float, float> {
-    static __device__ __forceinline__ float ld(const float *p) { return *p; }
-    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+    // L2-only loads and evict-first stores: the populations are streamed once
+    // per step (cache-policy choice measured on the 512^3 workload).
+    static __device__ __forceinline__ float ld(const float *p) { return __ldcg(p); }
+    static __device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
 };
 
 template <typename R> __device__ __forceinline__ R rcp_(R v);
@@ -50,32 +68,38 @@ template <typename R> __device__ __forceinline__ R sqrt_(R v);
 template <> __device__ __forceinline__ double sqrt_<double>(double v) { return sqrt(v); }
 template <> __device__ __forceinline__ float sqrt_<float>(float v) { return sqrtf(v); }
 
-// 1-D Hermite analysis of a 3-point line (values at c = -1, 0, +1):
-// (sum v, sum v c, sum v (c^2 - 1/3)).
+// ---------------------------------------------------------------------------
+// 1-D transforms (see lattice.cuh for the scales)
+
+// Hermite analysis of a 3-point line (values at c = -1, 0, +1):
+// (sum v, sum v c, 3 sum v (c^2 - 1/3)); the factor 3 is undone through the
+// host-side mode coefficients (fwd_scale).
 template <typename R>
 __device__ __forceinline__ void analyse(R &m, R &o, R &p)
 {
     const R s = m + p;
     const R d = p - m;
     const R h0 = s + o;
-    const R h2 = R(2.0 / 3.0) * s - R(1.0 / 3.0) * o;
+    const R h2 = R(2) * s - o;
     m = h0;
     o = d;
     p = h2;
 }
 
-// 1-D synthesis with the weights folded in: value at c of
-// w1(c) (q0 + q1 c + q2 (c^2 - 1/3)), written back as (c = -1, 0, +1).
+// Synthesis of prescaled amplitudes (syn_scale): the values at c = -1, 0, +1
+// of w1(c) (q0 + q1 c + q2 (c^2 - 1/3)) for the unscaled q.
 template <typename R>
-__device__ __forceinline__ void synthesise(R &q0, R &q1, R &q2)
+__device__ __forceinline__ void synthesise(R &p0, R &p1, R &p2)
 {
-    const R t = R(1.0 / 6.0) * q0 + R(1.0 / 9.0) * q2;    // w1(+-1) (q0 + 2/3 q2)
-    const R s = R(1.0 / 6.0) * q1;                         // w1(+-1) q1
-    const R z = R(2.0 / 3.0) * q0 - R(2.0 / 9.0) * q2;    // w1(0) (q0 - 1/3 q2)
-    q0 = t - s;
-    q1 = z;
-    q2 = t + s;
+    const R t = p0 + p2;
+    const R z = R(4) * p0 - R(2) * p2;
+    p0 = t - p1;
+    p2 = t + p1;
+    p1 = z;
 }
+
+// ---------------------------------------------------------------------------
+// reductions
 
 template <typename R>
 __device__ __forceinline__ R warp_sum(R v)
@@ -85,11 +109,13 @@ __device__ __forceinline__ R warp_sum(R v)
     return v;
 }
 
+// Per-CTA FP64 partials of the per-thread sums (blockDim.x a multiple of 32,
+// at most 32 warps).
 template <typename R>
 __device__ __forceinline__ void block_reduce_store(const R (&acc)[NSTAT], double *out)
 {
-    __shared__ double sh[kBlock / 32][NSTAT];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double sh[32][NSTAT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int s = 0; s < NSTAT; ++s) {
         const R v = warp_sum(acc[s]);
@@ -98,41 +124,19 @@ __device__ __forceinline__ void block_reduce_store(const R (&acc)[NSTAT], double
     __syncthreads();
     if (threadIdx.x < NSTAT) {
         double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < kBlock / 32; ++w) t += sh[w][threadIdx.x];
+        for (int w = 0; w < nw; ++w) t += sh[w][threadIdx.x];
         out[threadIdx.x] = t;
     }
 }
 
-template <typename S, typename R, int SCHEME, bool ODD, bool STATS>
-__device__ __forceinline__ void node_update(S *__restrict__ g, const StepArgs<R> &a, uint32_t x,
-                                            uint32_t y, uint32_t z, R (&acc)[NSTAT])
+// ---------------------------------------------------------------------------
+// a2-a7, a9: collision of one node.  v[cx+1][cy+1][cz+1] holds the incoming
+// deviations on entry and the post-collision deviations on exit.
+
+template <typename R, int SCHEME, bool STATS>
+__device__ __forceinline__ void collide_core(R (&v)[3][3][3], const StepArgs<R> &a, uint32_t node,
+                                             R (&acc)[NSTAT])
 {
-    const uint32_t nx = a.nx, ny = a.ny, nz = a.nz;
-    const uint64_t N = a.n;
-    const uint32_t xs[3] = {x ? x - 1 : nx - 1, x, (x + 1 < nx) ? x + 1 : 0};
-    const uint32_t ys[3] = {y ? y - 1 : ny - 1, y, (y + 1 < ny) ? y + 1 : 0};
-    const uint32_t zs[3] = {z ? z - 1 : nz - 1, z, (z + 1 < nz) ? z + 1 : 0};
-    const uint64_t n = xs[1] + uint64_t(nx) * (ys[1] + uint64_t(ny) * zs[1]);
-
-    // a1: load the 27 incoming populations, v[cx+1][cy+1][cz+1]
-    R v[3][3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                uint64_t idx;
-                if (!ODD) {
-                    idx = uint64_t(slot_of(i - 1, j - 1, k - 1)) * N + n;
-                } else {
-                    const uint64_t nb = xs[2 - i] + uint64_t(nx) * (ys[2 - j] + uint64_t(ny) * zs[2 - k]);
-                    idx = uint64_t(slot_of(1 - i, 1 - j, 1 - k)) * N + nb;
-                }
-                v[i][j][k] = Conv<S, R>::ld(g + idx);
-            }
-
     // a2: forward Hermite projection, three 1-D passes
 #pragma unroll
     for (int j = 0; j < 3; ++j)
@@ -154,13 +158,13 @@ __device__ __forceinline__ void node_update(S *__restrict__ g, const StepArgs<R>
     const R ux = jx * irho, uy = jy * irho, uz = jz * irho;
 
     if (!(rho > R(0)) || !(rho < R(INFINITY))) {
-        *a.flag = 1u;
+        atomicOr(a.flag, 1u);
         atomicMin(a.bad_step, (unsigned long long)a.step);
     }
 
     if (STATS) {
         const R m2 = jx + jy + jz;
-        const R m3 = v[2][0][0] + v[0][2][0] + v[0][0][2] + drho;
+        const R m3 = R(1.0 / 3.0) * (v[2][0][0] + v[0][2][0] + v[0][0][2]) + drho;
         const R m4 = v[1][1][0] + v[1][0][1] + v[0][1][1];
         acc[S_DRHO] += drho;
         acc[S_JX] += jx;
@@ -169,7 +173,6 @@ __device__ __forceinline__ void node_update(S *__restrict__ g, const StepArgs<R>
         acc[S_UX2] += ux * ux;
         acc[S_UY2] += uy * uy;
         acc[S_UZ2] += uz * uz;
-        acc[S_M2] += m2;
         acc[S_M3] += m3;
         acc[S_M4] += m4;
         acc[S_M1SQ] += drho * drho;
@@ -178,9 +181,10 @@ __device__ __forceinline__ void node_update(S *__restrict__ g, const StepArgs<R>
         acc[S_M4SQ] += m4 * m4;
     }
 
-    // a3-a5: post-collision mode amplitudes M, then Q = M / b_k
-    const R lam = a.lambda;
+    // a3-a5: post-collision amplitudes in the reconstruction's units,
+    // Q = syn_scale * M (coefficients in StepArgs, see mode_coefficients)
     R qm[3][3][3];
+    const R jj[3] = {jx, jy, jz};
     const R uu[3] = {ux, uy, uz};
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -189,57 +193,57 @@ __device__ __forceinline__ void node_update(S *__restrict__ g, const StepArgs<R>
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const int ord = mode_order(i, j, k);
-                R post;
+                const int mk = mode_of(i, j, k);
+                R q;
                 if (ord == 0) {
-                    post = drho;                      // deviation of M_0 = rho
+                    q = drho * R(syn_scale(0, 0, 0));          // deviation of M_0 = rho
                 } else if (ord == 1) {
-                    post = v[i][j][k];                // momentum, conserved
+                    q = v[i][j][k] * R(syn_scale(i, j, k));     // momentum, conserved
+                } else if (ord == 2 || SCHEME == 2) {
+                    // Maxwell-Boltzmann coefficient rho u_x^i u_y^j u_z^k
+                    // = j_first * (remaining u factors)
+                    const int first = i ? 0 : (j ? 1 : 2);
+                    R aeq = jj[first];
+                    const int rest[3] = {i - (first == 0), j - (first == 1), k - (first == 2)};
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+                        for (int e = 0; e < rest[ax]; ++e) aeq *= uu[ax];
+                    if (ord == 2) q = a.cq_m[mk] * v[i][j][k] + a.cq_eq[mk] * aeq;
+                    else q = a.cq_eq[mk] * aeq;                 // Reg ghosts
+                } else if (SCHEME == 0) {
+                    q = a.cq_m[mk] * v[i][j][k];                // BGK ghosts
                 } else {
-                    // Maxwell-Boltzmann Hermite coefficient rho u_x^i u_y^j u_z^k
-                    R aeq = rho;
-#pragma unroll
-                    for (int e = 0; e < i; ++e) aeq *= uu[0];
-#pragma unroll
-                    for (int e = 0; e < j; ++e) aeq *= uu[1];
-#pragma unroll
-                    for (int e = 0; e < k; ++e) aeq *= uu[2];
-                    if (ord == 2) {
-                        post = aeq + lam * (v[i][j][k] - aeq);
-                    } else if (SCHEME == 0) {             // BGK: 2nd-order f^eq
-                        post = lam * v[i][j][k];
-                    } else if (SCHEME == 2) {             // Reg: full-order f^eq
-                        post = aeq;
-                    } else {                              // GMF: filtered
-                        post = R(0);
-                    }
+                    q = R(0);                                   // GMF: filtered
                 }
-                qm[i][j][k] = post * R(1.0 / b_of(i, j, k));
+                qm[i][j][k] = q;
             }
 
-    // a6: FDT noise, M_k += phi_k r_k for k = 4..26 (in Q units: / b_k)
+    // a6: FDT noise, M_k += phi_k r_k for k = 4..26; each pair of normals is
+    // folded in as soon as it is drawn
     {
         const R sr = a.noise_rho0 ? a.sqrt_rho0 : sqrt_(rho);
-        R r[28];
 #pragma unroll
         for (int blk = 0; blk < 6; ++blk) {
             const u32x4 o = philox4x32_10(
-                u32x4{uint32_t(n), uint32_t(a.step), uint32_t(blk), uint32_t(a.step >> 32)},
-                a.key0, a.key1);
-            box_muller(o.x, o.y, r[4 + 4 * blk], r[5 + 4 * blk]);
-            box_muller(o.z, o.w, r[6 + 4 * blk], r[7 + 4 * blk]);
-        }
+                u32x4{node, uint32_t(a.step), uint32_t(blk), uint32_t(a.step >> 32)}, a.rk);
+            R rad0, c0, s0, rad1, c1, s1;
+            box_muller(o.x, o.y, rad0, c0, s0);
+            box_muller(o.z, o.w, rad1, c1, s1);
+            const R sc0 = sr * rad0, sc1 = sr * rad1;
+            const R trig[4] = {c0, s0, c1, s1};
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const int mk = mode_of(i, j, k);
-                    if (mk >= 4) qm[i][j][k] += (sr * a.nc[mk]) * r[mk];
+            for (int m = 0; m < 4; ++m) {
+                const int mk = 4 + 4 * blk + m;
+                if (mk < kQ) {
+                    const int d = mode_deg(mk);
+                    qm[d % 3][(d / 3) % 3][d / 9] += ((m < 2 ? sc0 : sc1) * trig[m]) * a.ncq[mk];
                 }
+            }
+        }
     }
 
-    // a7: reconstruction f*_i - w_i rho0 = w_i sum_k e_ki Q_k (Q_0 = drho)
+    // a7: reconstruction f*_i - w_i rho0 = w_i sum_k e_ki M_k / b_k (M_0 -> drho)
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -253,47 +257,345 @@ __device__ __forceinline__ void node_update(S *__restrict__ g, const StepArgs<R>
 #pragma unroll
         for (int k = 0; k < 3; ++k) synthesise(qm[0][j][k], qm[1][j][k], qm[2][j][k]);
 
-    // a8: AA store
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                uint64_t idx;
-                if (!ODD) {
-                    idx = uint64_t(slot_of(1 - i, 1 - j, 1 - k)) * N + n;
-                } else {
-                    const uint64_t nb = xs[i] + uint64_t(nx) * (ys[j] + uint64_t(ny) * zs[k]);
-                    idx = uint64_t(slot_of(i - 1, j - 1, k - 1)) * N + nb;
-                }
-                Conv<S, R>::st(g + idx, qm[i][j][k]);
-            }
+            for (int k = 0; k < 3; ++k) v[i][j][k] = qm[i][j][k];
 }
 
-template <typename S, typename R, int SCHEME, bool ODD, bool STATS>
-__global__ void __launch_bounds__(kBlock) k_step(S *__restrict__ g, const StepArgs<R> a)
+// ---------------------------------------------------------------------------
+// k_step: one thread per node, direct loads/stores (general boxes)
+
+// Periodic neighbour offsets of node (x,y,z): xs[d], ry[d], rz[d] for the
+// displacements d-1 = -1, 0, +1 along each axis (node index = xs + ry + rz).
+template <typename I>
+struct Nbr {
+    I xs[3], ry[3], rz[3];
+    __device__ __forceinline__ Nbr(uint32_t x, uint32_t y, uint32_t z, uint32_t nx, uint32_t ny,
+                                   uint32_t nz)
+    {
+        const I plane = I(nx) * I(ny);
+        xs[0] = I(x ? x - 1 : nx - 1);
+        xs[1] = I(x);
+        xs[2] = I((x + 1 < nx) ? x + 1 : 0);
+        ry[0] = I(y ? y - 1 : ny - 1) * I(nx);
+        ry[1] = I(y) * I(nx);
+        ry[2] = I((y + 1 < ny) ? y + 1 : 0) * I(nx);
+        rz[0] = I(z ? z - 1 : nz - 1) * plane;
+        rz[1] = I(z) * plane;
+        rz[2] = I((z + 1 < nz) ? z + 1 : 0) * plane;
+    }
+    __device__ __forceinline__ I node() const { return xs[1] + ry[1] + rz[1]; }
+};
+
+template <typename S, typename R, typename I, int SCHEME, bool ODD, bool STATS>
+__global__ void __launch_bounds__(kBlock, FLBM_MIN_BLOCKS) k_step(S *__restrict__ g, const StepArgs<R> a)
 {
     R acc[NSTAT];
 #pragma unroll
     for (int s = 0; s < NSTAT; ++s) acc[s] = R(0);
+    const I N = I(a.n);
     for (uint64_t ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x) {
         const uint32_t xc = uint32_t(ch % a.cpr);
         const uint64_t r = ch / a.cpr;
         const uint32_t y = uint32_t(r % a.ny);
         const uint32_t z = uint32_t(r / a.ny);
         const uint32_t x = xc * kBlock + threadIdx.x;
-        if (x < a.nx) node_update<S, R, SCHEME, ODD, STATS>(g, a, x, y, z, acc);
+        if (x >= a.nx) continue;
+        const Nbr<I> nb(x, y, z, a.nx, a.ny, a.nz);
+        const I n = nb.node();
+        // a1: load
+        R v[3][3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    I idx;
+                    if (!ODD) idx = I(slot_of(i - 1, j - 1, k - 1)) * N + n;
+                    else idx = I(slot_of(1 - i, 1 - j, 1 - k)) * N + (nb.xs[2 - i] + nb.ry[2 - j] + nb.rz[2 - k]);
+                    v[i][j][k] = Conv<S, R>::ld(g + idx);
+                }
+        collide_core<R, SCHEME, STATS>(v, a, uint32_t(n), acc);
+        // a8: AA store
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    I idx;
+                    if (!ODD) idx = I(slot_of(1 - i, 1 - j, 1 - k)) * N + n;
+                    else idx = I(slot_of(i - 1, j - 1, k - 1)) * N + (nb.xs[i] + nb.ry[j] + nb.rz[k]);
+                    Conv<S, R>::st(g + idx, v[i][j][k]);
+                }
     }
     if (STATS) block_reduce_store(acc, a.partials + size_t(blockIdx.x) * NSTAT);
 }
 
-template <typename S, typename R>
-cudaError_t launch_step_t(S *g, const StepArgs<R> &a, int scheme, bool odd, bool stats, int grid,
-                          cudaStream_t s)
+// ---------------------------------------------------------------------------
+// k_step_rows: TMA bulk-copy row pipeline
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-#define FLBM_LAUNCH(SC, OD, ST) \
-    k_step<S, R, SC, OD, ST><<<grid, kBlock, 0, s>>>(g, a)
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Bounded wait for the phase with the given parity: false after 2^22 polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t addr = smem_u32(bar);
+    for (uint32_t it = 0; it < (1u << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n"
+            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// global -> shared bulk copy completing on an mbarrier (16-byte aligned
+// addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst),
+                 "r"(smem_u32(src)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all()
+{
+    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+constexpr int kRowCompute = 256;   // max compute threads of a row CTA (8 warps)
+constexpr int kRowStages = 2;      // shared-memory stages (rows in flight)
+
+// Shared staging of a row CTA per stage: 27 segments of nx elements.
+template <typename S>
+__host__ __device__ constexpr size_t row_stage_bytes(uint32_t nx) { return size_t(kQ) * nx * sizeof(S); }
+
+// Global segment (plane slot, row) of segment index d = 9 (cx+1) + 3 (cy+1) +
+// (cz+1) for the row (y, z): the even form reads slot c of the row itself,
+// the odd form slot opp(c) of row (y - cy, z - cz).  The same segment later
+// receives the post-collision values of direction -c.
+template <typename S, typename R, bool ODD>
+__device__ __forceinline__ S *row_segment(S *g, const StepArgs<R> &a, int d, uint64_t row)
+{
+    const uint32_t y = uint32_t(row % a.ny), z = uint32_t(row / a.ny);
+    const int cx = d / 9 - 1, cy = (d / 3) % 3 - 1, cz = d % 3 - 1;
+    uint32_t yy = y, zz = z;
+    int slot = slot_of(cx, cy, cz);
+    if (ODD) {
+        slot = slot_of(-cx, -cy, -cz);
+        if (cy > 0) yy = y ? y - 1 : a.ny - 1;
+        if (cy < 0) yy = (y + 1 < a.ny) ? y + 1 : 0;
+        if (cz > 0) zz = z ? z - 1 : a.nz - 1;
+        if (cz < 0) zz = (z + 1 < a.nz) ? z + 1 : 0;
+    }
+    return g + (uint64_t(slot) * a.n + (uint64_t(zz) * a.ny + yy) * a.nx);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp-specialised row pipeline.  Warps 0..nc/32-1 collide; the last warp
+// is the producer: its lanes 0..26 each move one of the 27 segments of a row
+// (bulk load into stage k % kRowStages, completing on full[s]; after the
+// compute warps release the stage through empty[s], bulk store back to HBM).
+// Every wait is bounded; a wait that runs out sets flag bit 1 and stops.
+template <typename S, typename R, int SCHEME, bool ODD, bool STATS>
+__global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) == 4 ? 2 : 1)
+    k_step_rows(S *__restrict__ g, const StepArgs<R> a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kRowStages], empty[kRowStages];
+    S *const stage = reinterpret_cast<S *>(smem_raw);
+    const uint32_t nx = a.nx;
+    const uint32_t nc = blockDim.x - 32;                  // compute threads
+    const uint32_t stage_elems = uint32_t(kQ) * nx;
+    const uint32_t seg_bytes = nx * uint32_t(sizeof(S));
+    const uint64_t nrows = uint64_t(a.ny) * a.nz;
+    const uint32_t lane = threadIdx.x & 31;
+    R acc[NSTAT];
+#pragma unroll
+    for (int s = 0; s < NSTAT; ++s) acc[s] = R(0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kRowStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], nc / 32);
+        }
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    if (threadIdx.x >= nc) {
+        // ---------------- producer warp ----------------
+        const int d = int(lane);
+        uint64_t k = 0;
+        bool ok = true;
+        // store of row number kk (this CTA's kk-th row) out of its stage
+        auto store_row = [&](uint64_t kk) {
+            const int s = int(kk % kRowStages);
+            ok = mbar_wait(&empty[s], uint32_t((kk / kRowStages) & 1));
+            if (!ok) return;
+            const uint64_t row = blockIdx.x + kk * gridDim.x;
+            if (d < kQ) {
+                bulk_s2g(row_segment<S, R, ODD>(g, a, d, row), stage + size_t(s) * stage_elems + d * nx,
+                         seg_bytes);
+                bulk_commit();
+                bulk_wait_read_all();
+            }
+            __syncwarp();
+        };
+        for (;; ++k) {
+            const uint64_t row = blockIdx.x + k * gridDim.x;
+            if (row >= nrows) break;
+            const int s = int(k % kRowStages);
+            if (k >= kRowStages) {
+                store_row(k - kRowStages);
+                if (!ok) break;
+            }
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&full[s], uint32_t(kQ) * seg_bytes);
+            }
+            __syncwarp();
+            if (d < kQ)
+                bulk_g2s(stage + size_t(s) * stage_elems + d * nx, row_segment<S, R, ODD>(g, a, d, row),
+                         seg_bytes, &full[s]);
+        }
+        // drain the last stages
+        for (uint64_t kk = (k > kRowStages ? k - kRowStages : 0); ok && kk < k; ++kk) store_row(kk);
+        if (!ok && lane == 0) atomicOr(a.flag, 2u);
+        if (d < kQ) bulk_wait_all();
+    } else {
+        // ---------------- compute warps ----------------
+        for (uint64_t k = 0;; ++k) {
+            const uint64_t row = blockIdx.x + k * gridDim.x;
+            if (row >= nrows) break;
+            const int s = int(k % kRowStages);
+            if (!mbar_wait(&full[s], uint32_t((k / kRowStages) & 1))) {
+                if (lane == 0) atomicOr(a.flag, 2u);
+                break;
+            }
+            const uint32_t y = uint32_t(row % a.ny), z = uint32_t(row / a.ny);
+            S *st = stage + size_t(s) * stage_elems;
+            for (uint32_t x = threadIdx.x; x < nx; x += nc) {
+                const uint32_t xsh[3] = {x ? x - 1 : nx - 1, x, (x + 1 < nx) ? x + 1 : 0};
+                // a1: incoming f_c(x) from segment d(c) at x (even) / x - c_x (odd)
+                R v[3][3][3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+#pragma unroll
+                        for (int kk = 0; kk < 3; ++kk) {
+                            const uint32_t pos = ODD ? xsh[2 - i] : x;
+                            v[i][j][kk] = R(st[(9 * i + 3 * j + kk) * nx + pos]);
+                        }
+                collide_core<R, SCHEME, STATS>(v, a, x + nx * (y + a.ny * z), acc);
+                // a8: f*_c(x) to segment d(-c) at x (even) / x + c_x (odd)
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+#pragma unroll
+                        for (int kk = 0; kk < 3; ++kk) {
+                            const uint32_t pos = ODD ? xsh[i] : x;
+                            st[(9 * (2 - i) + 3 * (2 - j) + (2 - kk)) * nx + pos] = S(v[i][j][kk]);
+                        }
+            }
+            fence_proxy_async_smem();   // generic-proxy writes before the bulk store reads
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+    }
+    if (STATS) block_reduce_store(acc, a.partials + size_t(blockIdx.x) * NSTAT);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+// Whether the row pipeline serves a box of row length nx, and its CTA shape.
+struct RowPlan {
+    bool use = false;
+    int threads = 0;
+    size_t smem = 0;
+};
+template <typename S>
+inline RowPlan row_plan(uint32_t nx)
+{
+    RowPlan p;
+    const size_t smem = kRowStages * row_stage_bytes<S>(nx);
+    if (nx % 32 != 0 || nx < 32 || smem > 200 * 1024) return p;
+    const uint32_t npt = (nx + kRowCompute - 1) / kRowCompute;
+    uint32_t thr = (nx + npt - 1) / npt;
+    thr = (thr + 31) / 32 * 32;
+    p.use = true;
+    p.threads = int(thr) + 32;   // compute warps + the producer warp
+    p.smem = smem;
+    return p;
+}
+
+template <typename S, typename R, typename I>
+cudaError_t launch_step_t(S *g, const StepArgs<R> &a, int scheme, bool odd, bool stats, int grid,
+                          int row_grid, cudaStream_t s)
+{
+    const RowPlan rp = row_plan<S>(a.nx);
+    if (rp.use && row_grid > 0) {
+#define FLBM_LAUNCH_ROWS(SC, OD, ST) \
+    k_step_rows<S, R, SC, OD, ST><<<row_grid, rp.threads, rp.smem, s>>>(g, a)
+        if (scheme == 0) {
+            if (odd) { if (stats) FLBM_LAUNCH_ROWS(0, true, true); else FLBM_LAUNCH_ROWS(0, true, false); }
+            else     { if (stats) FLBM_LAUNCH_ROWS(0, false, true); else FLBM_LAUNCH_ROWS(0, false, false); }
+        } else if (scheme == 1) {
+            if (odd) { if (stats) FLBM_LAUNCH_ROWS(1, true, true); else FLBM_LAUNCH_ROWS(1, true, false); }
+            else     { if (stats) FLBM_LAUNCH_ROWS(1, false, true); else FLBM_LAUNCH_ROWS(1, false, false); }
+        } else {
+            if (odd) { if (stats) FLBM_LAUNCH_ROWS(2, true, true); else FLBM_LAUNCH_ROWS(2, true, false); }
+            else     { if (stats) FLBM_LAUNCH_ROWS(2, false, true); else FLBM_LAUNCH_ROWS(2, false, false); }
+        }
+#undef FLBM_LAUNCH_ROWS
+        return cudaGetLastError();
+    }
+#define FLBM_LAUNCH(SC, OD, ST) k_step<S, R, I, SC, OD, ST><<<grid, kBlock, 0, s>>>(g, a)
     if (scheme == 0) {
         if (odd) { if (stats) FLBM_LAUNCH(0, true, true); else FLBM_LAUNCH(0, true, false); }
         else     { if (stats) FLBM_LAUNCH(0, false, true); else FLBM_LAUNCH(0, false, false); }
@@ -308,22 +610,38 @@ cudaError_t launch_step_t(S *g, const StepArgs<R> &a, int scheme, bool odd, bool
     return cudaGetLastError();
 }
 
-template <typename S, typename R>
-int step_occupancy_t(int scheme, bool stats)
+// Resident CTAs per SM of the larger (reducing, odd-form) variant of each
+// kernel; also opts the row kernels into their shared memory on the current
+// device.  rows = 0 when the row pipeline does not serve the box.
+template <typename S, typename R, typename I, int SC>
+void prepare_scheme(uint32_t nx, bool stats, int &direct, int &rows)
 {
+    direct = 1;
+    rows = 0;
     int nb = 0;
-    cudaError_t e;
-    // the odd form has the larger register footprint; use it for both
-    if (scheme == 0)
-        e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<S, R, 0, true, true>, kBlock, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<S, R, 0, true, false>, kBlock, 0);
-    else if (scheme == 1)
-        e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<S, R, 1, true, true>, kBlock, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<S, R, 1, true, false>, kBlock, 0);
-    else
-        e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<S, R, 2, true, true>, kBlock, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<S, R, 2, true, false>, kBlock, 0);
-    return (e == cudaSuccess && nb > 0) ? nb : 1;
+    cudaError_t e = stats
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<S, R, I, SC, true, true>, kBlock, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<S, R, I, SC, true, false>, kBlock, 0);
+    if (e == cudaSuccess && nb > 0) direct = nb;
+    const RowPlan rp = row_plan<S>(nx);
+    if (!rp.use) return;
+    const int sm = int(rp.smem);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    nb = 0;
+    e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<S, R, SC, true, true>, rp.threads, rp.smem)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<S, R, SC, true, false>, rp.threads, rp.smem);
+    if (e == cudaSuccess && nb > 0) rows = nb;
+}
+
+template <typename S, typename R, typename I>
+void step_occupancy_t(int scheme, uint32_t nx, bool stats, int &direct, int &rows)
+{
+    if (scheme == 0) prepare_scheme<S, R, I, 0>(nx, stats, direct, rows);
+    else if (scheme == 1) prepare_scheme<S, R, I, 1>(nx, stats, direct, rows);
+    else prepare_scheme<S, R, I, 2>(nx, stats, direct, rows);
 }
 
 }  // namespace flbm
