@@ -200,6 +200,37 @@ int flbm_get_params(const flbm_ctx *c, flbm_params *out);
  * next call on c); c == NULL gives the thread's last create-time error. */
 const char *flbm_last_error(const flbm_ctx *c);
 
+/* One fused step (the kernels of flbm_step) on caller-owned device memory,
+ * with no device allocation: for callers that cannot let a library allocate
+ * GPU memory, e.g. applications whose own allocator owns every byte of the
+ * device, or a host program that embeds the solver under a fixed memory
+ * budget.  The paper has no counterpart; this is a deployment interface.
+ *
+ *   p          box, scheme, tau, kT, rho0, seed, noise_rho0; precision must be
+ *              FLBM_FP32 (FLBM_E_UNSUPPORTED otherwise); stats_every ignored.
+ *   dev_state  27 N floats of deviations g_i = f_i - w_i rho0, SoA planes,
+ *              256-byte aligned, updated in place (AA pattern).
+ *   step       time index t of this collision (the noise counter).
+ *   parity     storage form of dev_state on entry: 0 natural (slot i of node
+ *              x holds f_i(x)), 1 AA-shifted; the call leaves the other form.
+ *   dev_sums   13 doubles of device memory receiving the global sums over the
+ *              pre-collision state at t: drho, jx, jy, jz, ux^2, uy^2, uz^2,
+ *              m3, m4, drho^2, (sum_a j_a)^2, m3^2, m4^2 with m3 = sum_a Pi_aa
+ *              - rho0, m4 = sum_{a<b} Pi_ab.
+ *   cuda_stream stream the work is ordered on (NULL: the legacy stream); the
+ *              call returns after the step completed.
+ * Scratch (per-CTA partial sums and flags) lives in one static device array
+ * of 208 KiB that every GPU loading the library keeps until process exit;
+ * a launch needing more than its 2048 CTA slots is rejected with
+ * FLBM_E_INVALID.  The first call on a device resolves that array's address
+ * (cudaGetSymbolAddress) with the device current; make it before any stream
+ * capture.  Every call reuses the same array, so calls that overlap on the
+ * GPU (other streams, other threads) race and must be serialised by the
+ * caller.  Errors: FLBM_E_INVALID, FLBM_E_UNSUPPORTED, FLBM_E_CUDA,
+ * FLBM_E_UNSTABLE, FLBM_E_TIMEOUT; text via flbm_last_error(NULL). */
+int flbm_step_noalloc(const flbm_params *p, void *dev_state, int64_t step, int parity,
+                      double *dev_sums, void *cuda_stream);
+
 /* Release everything the context owns (not a caller dev_buf/stream). */
 void flbm_destroy(flbm_ctx *c);
 

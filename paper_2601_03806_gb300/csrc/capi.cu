@@ -165,6 +165,24 @@ void mode_coefficients(const flbm_params &p, StepArgs<R> &a)
 }
 
 template <typename R>
+void fill_constants_t(const flbm_params &p, StepArgs<R> &a)
+{
+    // Philox4x32-10 key schedule: key = seed, bumped by the Weyl constants
+    // (0x9E3779B9, 0xBB67AE85) before each round after the first
+    uint32_t k0 = uint32_t(p.seed & 0xffffffffu), k1 = uint32_t(p.seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        a.rk[2 * r] = k0;
+        a.rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    a.noise_rho0 = p.noise_rho0;
+    a.rho0 = R(p.rho0);
+    a.sqrt_rho0 = R(std::sqrt(p.rho0));
+    mode_coefficients<R>(p, a);
+}
+
+template <typename R>
 StepArgs<R> make_args(const flbm_ctx *c, int64_t t)
 {
     StepArgs<R> a;
@@ -176,19 +194,7 @@ StepArgs<R> make_args(const flbm_ctx *c, int64_t t)
     a.n = c->n;
     a.nchunks = uint64_t(a.cpr) * a.ny * a.nz;
     a.step = uint64_t(t);
-    // Philox4x32-10 key schedule: key = seed, bumped by the Weyl constants
-    // (0x9E3779B9, 0xBB67AE85) before each round after the first
-    uint32_t k0 = uint32_t(c->p.seed & 0xffffffffu), k1 = uint32_t(c->p.seed >> 32);
-    for (int r = 0; r < 10; ++r) {
-        a.rk[2 * r] = k0;
-        a.rk[2 * r + 1] = k1;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    a.noise_rho0 = c->p.noise_rho0;
-    a.rho0 = R(c->p.rho0);
-    a.sqrt_rho0 = R(std::sqrt(c->p.rho0));
-    mode_coefficients<R>(c->p, a);
+    fill_constants_t<R>(c->p, a);
     a.partials = c->partials;
     a.flag = &c->dflags->flag;
     a.bad_step = &c->dflags->bad_step;
@@ -317,6 +323,12 @@ int create_impl(const flbm_params *p, void *dev_buf, size_t dev_bytes, void *str
 }
 
 }  // namespace
+
+namespace flbm {
+void fill_step_constants(const flbm_params &p, StepArgs<float> &a) { fill_constants_t<float>(p, a); }
+void fill_step_constants(const flbm_params &p, StepArgs<double> &a) { fill_constants_t<double>(p, a); }
+void set_thread_error(const char *msg) { g_create_error = msg; }
+}  // namespace flbm
 
 extern "C" {
 

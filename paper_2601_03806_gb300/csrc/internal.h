@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct flbm_params;
+
 namespace flbm {
 
 constexpr int kQ = 27;
@@ -70,6 +72,14 @@ cudaError_t launch_step_f32(float *g, const StepArgs<float> &a, int scheme, bool
 // prepares the kernels' shared-memory attributes on the current device.
 void step_occupancy_f64(int scheme, uint32_t nx, bool stats, int &direct, int &rows);
 void step_occupancy_f32(int scheme, uint32_t nx, uint64_t n, bool stats, int &direct, int &rows);
+
+// Step constants shared by flbm_step and flbm_step_noalloc (capi.cu): the
+// Philox round keys, the density used by the noise, and the per-mode
+// relaxation / equilibrium / noise coefficients of the scheme.
+void fill_step_constants(const flbm_params &p, StepArgs<float> &a);
+void fill_step_constants(const flbm_params &p, StepArgs<double> &a);
+// Set the calling thread's error text returned by flbm_last_error(NULL).
+void set_thread_error(const char *msg);
 
 // Auxiliary kernels (aux.cu).  `prec` is 0 (double storage) or 1 (float).
 struct BoxDesc {

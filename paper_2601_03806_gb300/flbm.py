@@ -82,6 +82,7 @@ def _load():
         "flbm_get_params": ([vp, P(flbm_params)], i32),
         "flbm_last_error": ([vp], C.c_char_p),
         "flbm_destroy": ([vp], None),
+        "flbm_step_noalloc": ([P(flbm_params), vp, i64, i32, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -114,6 +115,7 @@ flbm_set_step = lib.flbm_set_step
 flbm_get_params = lib.flbm_get_params
 flbm_last_error = lib.flbm_last_error
 flbm_destroy = lib.flbm_destroy
+flbm_step_noalloc = lib.flbm_step_noalloc
 
 
 def _ptr(a: np.ndarray):
