@@ -31,9 +31,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(nx=512, ny=512, nz=512, tau=0.6, kT=1e-5, rho0=1.0, seed=20260101, scheme="gmf")
-BYTES_PER_NODE = 27 * 4 * 2          # FP32 populations: 27 reads + 27 writes per update
+# algorithmic HBM bytes per lattice update: 27 reads + 27 writes of the
+# storage type
+BYTES_PER_NODE = {"fp32": 27 * 4 * 2, "fp16": 27 * 2 * 2, "fp64": 27 * 8 * 2}
 CS2 = 1.0 / 3.0
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_f32_gmf_traffic.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_rows_f32_gmf_traffic.txt")
 KERNEL_SOURCES = ["step_kernel.cuh", "lattice.cuh", "internal.h", "step_f32.cu"]
 
 
@@ -44,6 +46,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=512, help="cube edge (512 = the benchmark workload)")
+    ap.add_argument("--precision", choices=["fp32", "fp16", "fp64"], default="fp32",
+                    help="population storage (fp32 = the benchmark workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args(argv)
@@ -188,20 +192,6 @@ def recorded_traffic(size: int):
         return None
 
 
-def thermal_fill(lat, n, kT, rho0, seed):
-    """Seeded sample of the invariant measure written straight into the
-    torch-owned population buffer (natural form at step 0)."""
-    import torch
-    import oracle
-    w = oracle.tables()["w"]
-    buf = lat._buf.view(torch.float32).view(27, -1)
-    gen = torch.Generator(device=buf.device)
-    gen.manual_seed(seed)
-    for i in range(27):
-        buf[i].normal_(0.0, float((rho0 * kT * w[i] / CS2) ** 0.5), generator=gen)
-    torch.cuda.synchronize()
-
-
 def host_mem_available() -> int:
     try:
         for ln in open("/proc/meminfo"):
@@ -280,13 +270,16 @@ def metric_name():
     return "MLUPS of the fused GMF-FLBM D3Q27 stream-and-collide step (HBM roofline fraction beside it)"
 
 
-def workload_config(size, ws):
-    return {"workload": "GMF-FLBM D3Q27 periodic %d^3, FP32 deviation populations AA in place, "
-                        "rho0=1, kT=1e-5, tau=0.6, FP64 reductions every step" % size,
+def workload_config(size, ws, precision="fp32"):
+    es = BYTES_PER_NODE[precision] // 54
+    return {"workload": "GMF-FLBM D3Q27 periodic %d^3, %s deviation populations AA in place, "
+                        "rho0=1, kT=1e-5, tau=0.6, FP64 reductions every step"
+                        % (size, precision.upper()),
             "nx": size, "ny": size, "nz": size, "tau": WORKLOAD["tau"], "kT": WORKLOAD["kT"],
-            "rho0": WORKLOAD["rho0"], "scheme": "gmf", "storage": "fp32 deviations, AA in place",
+            "rho0": WORKLOAD["rho0"], "scheme": "gmf",
+            "storage": "%s deviations, AA in place" % precision,
             "stats_every": 1, "l2": "inputs larger than L2 (%.1f GB state vs 129 MB L2)"
-            % (27 * 4 * size ** 3 / 1e9),
+            % (27 * es * size ** 3 / 1e9),
             "parallelism": "replicas x%d (one independent box per GPU)" % ws}
 
 
@@ -304,9 +297,11 @@ def run_ours(args, rank, local, ws):
     tau, kT, rho0 = WORKLOAD["tau"], WORKLOAD["kT"], WORKLOAD["rho0"]
     seed = WORKLOAD["seed"] + rank
     stream = torch.cuda.Stream(device=dev)
-    lat = flbm.Lattice(n, n, n, tau, kT, rho0=rho0, seed=seed, precision=flbm.FLBM_FP32,
+    prec = {"fp32": flbm.FLBM_FP32, "fp16": flbm.FLBM_FP16, "fp64": flbm.FLBM_FP64}[args.precision]
+    es = BYTES_PER_NODE[args.precision] // 54
+    lat = flbm.Lattice(n, n, n, tau, kT, rho0=rho0, seed=seed, precision=prec,
                        stats_every=1, torch_memory=True, stream=stream)
-    thermal_fill(lat, n, kT, rho0, seed)
+    lat.init_thermal(seed)           # invariant-measure start (library kernel)
     lat.step(args.warmup)
     lat.stats_reset()
     props = torch.cuda.get_device_properties(dev)
@@ -333,12 +328,18 @@ def run_ours(args, rank, local, ws):
 
     k_ms = kernel_ms / max(launches, 1)
     peak, peak_src = measured_hbm_peak()
-    achieved = BYTES_PER_NODE * N / (k_ms / 1e3) / 1e9
-    traffic = recorded_traffic(n)
+    achieved = BYTES_PER_NODE[args.precision] * N / (k_ms / 1e3) / 1e9
+    traffic = recorded_traffic(n) if args.precision == "fp32" else None
+    rows_path = n % 32 == 0 and 2 * 27 * n * es <= 200 * 1024 and os.environ.get("FLBM_ROWS", "1") != "0"
+    st_name = {"fp32": "float", "fp16": "__half", "fp64": "double"}[args.precision]
+    kname = ("flbm::k_step_rows<%s,GMF,*,stats> (TMA row pipeline)" % st_name if rows_path
+             else "flbm::k_step<%s,GMF,*,stats> (direct)" % st_name)
+    if not rows_path:
+        traffic = None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
-                "traffic": traffic, "kernel": "flbm::k_step<float,float,GMF,*,stats>",
-                "kernel_ms": k_ms, "algorithmic_bytes_per_launch": BYTES_PER_NODE * N}
+                "traffic": traffic, "kernel": kname,
+                "kernel_ms": k_ms, "algorithmic_bytes_per_launch": BYTES_PER_NODE[args.precision] * N}
 
     u2_ratio = [x / (kT / rho0) for x in st["u2_avg"]]
 
@@ -346,10 +347,11 @@ def run_ours(args, rank, local, ws):
     # each followed by a stats read, then one moments snapshot to the host.
     e2e = None
     if not args.no_e2e:
-        state_bytes = 27 * 4 * N
+        state_bytes = 27 * es * N
         mom_bytes = 10 * 8 * N
         with_moments = host_mem_available() > 3 * (state_bytes + mom_bytes)
-        hstate = torch.empty(27 * N, dtype=torch.float32, pin_memory=True)
+        tdt = {"fp32": torch.float32, "fp16": torch.float16, "fp64": torch.float64}[args.precision]
+        hstate = torch.empty(27 * N, dtype=tdt, pin_memory=True)
         lat.get_state(hstate)
         if with_moments:
             hrho = torch.empty(N, dtype=torch.float64, pin_memory=True)
@@ -391,8 +393,9 @@ def run_ours(args, rank, local, ws):
         line = {
             "metric": metric_name(), "value": value, "unit": "MLUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": workload_config(n, ws), "roofline": roofline,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp16": "f16 storage / f32 arithmetic", "fp64": "f64"}[args.precision],
+            "data": "synthetic", "config": workload_config(n, ws, args.precision), "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches) + int(args.steps),
             "clocks": clk.summary(),

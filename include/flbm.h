@@ -59,8 +59,9 @@ enum flbm_scheme { FLBM_BGK = 0, FLBM_GMF = 1, FLBM_REG = 2 };
  * FLBM_FP64: deviations g_i = f_i - w_i rho0 in double, FP64 arithmetic.
  * FLBM_FP32: deviations in float, FP32 arithmetic (FP64 only for the global
  *            reductions and the S(k) accumulators).
- * FLBM_FP16: deviations in half, FP32 arithmetic (not built yet:
- *            FLBM_E_UNSUPPORTED). */
+ * FLBM_FP16: deviations in half (IEEE binary16, round to nearest), FP32
+ *            arithmetic, FP64 reductions: 108 B of HBM traffic per lattice
+ *            update instead of 216 B.  Raw-state calls use 16-bit halves. */
 enum flbm_precision { FLBM_FP64 = 0, FLBM_FP32 = 1, FLBM_FP16 = 2 };
 
 enum flbm_status {
@@ -170,6 +171,19 @@ int flbm_structure_factor(flbm_ctx *c, int observable, int nshell, double *S,
 int flbm_get_populations(flbm_ctx *c, double *f);
 int flbm_set_populations(flbm_ctx *c, const double *f);
 
+/* Replace the state by a sample of the lattice ideal-gas invariant measure
+ * of the fluctuating dynamics: independent Gaussian deviations
+ * g_i(x) = sqrt(rho0 kT w_i / c_s^2) xi_i(x), xi ~ N(0,1), the stationary
+ * population statistics that make every Hermite mode k carry its
+ * equilibrium variance rho0 kT b_k / c_s^2 (the fluctuation-dissipation
+ * balance behind Eqs. fluct_phi / fluct_phig).  Starting there skips the
+ * thermalisation transient.  xi comes from Philox4x32-10 with key = seed and
+ * counter (node, 0, block 6 + j, 0), j = 0..6, disjoint from the step noise
+ * (blocks 0..5); Box-Muller on word pairs as for the noise; population i
+ * takes normal i of the node.  The step counter is kept; storage is left in
+ * the natural form. */
+int flbm_init_thermal(flbm_ctx *c, uint64_t seed);
+
 /* Absolute populations f_i(x, t) at `count` listed nodes (node indices n in
  * [0, N)), written as f[k*27 + i] for the k-th listed node: a probe for
  * large boxes where a full readback is impractical.  FLBM_E_INVALID if a
@@ -177,7 +191,8 @@ int flbm_set_populations(flbm_ctx *c, const double *f);
 int flbm_probe(flbm_ctx *c, const int64_t *nodes, int64_t count, double *f);
 
 /* Raw state: deviations g_i = f_i - w_i rho0 in the storage type (double for
- * FLBM_FP64, float for FLBM_FP32), SoA natural layout, 27 N elements.
+ * FLBM_FP64, float for FLBM_FP32, IEEE half for FLBM_FP16), SoA natural
+ * layout, 27 N elements.
  * Checkpoint = get_state + flbm_get_step; restore = set_state + set_step. */
 int flbm_get_state(flbm_ctx *c, void *host);
 int flbm_set_state(flbm_ctx *c, const void *host);

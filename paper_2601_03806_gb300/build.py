@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libflbm.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["capi.cu", "aux.cu", "step_f32.cu", "step_f64.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "aux.cu", "step_f32.cu", "step_f64.cu", "step_f16.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I" + os.path.join(ROOT, "include")]

@@ -2,6 +2,10 @@
 // populations, moment export (Eqs. rho/u and Pi), observable fields and the
 // FP64 shell binning of S(k) (Sec. III), and the final pass of the fused
 // reductions.
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "internal.h"
 #include "lattice.cuh"
 
@@ -39,15 +43,25 @@ __device__ __forceinline__ uint64_t storage_index(int cx, int cy, int cz, uint32
     return uint64_t(slot_of(-cx, -cy, -cz)) * b.n + n;
 }
 
+// storage element <-> double
 template <typename S>
-__device__ __forceinline__ double ldd(const S *g, uint64_t i) { return double(g[i]); }
+__device__ __forceinline__ double to_d(S v) { return double(v); }
+template <>
+__device__ __forceinline__ double to_d<__half>(__half v) { return double(__half2float(v)); }
+template <typename S>
+__device__ __forceinline__ S from_d(double v) { return S(v); }
+template <>
+__device__ __forceinline__ __half from_d<__half>(double v) { return __float2half_rn(float(v)); }
+
+template <typename S>
+__device__ __forceinline__ double ldd(const S *g, uint64_t i) { return to_d(g[i]); }
 
 template <typename S>
 __global__ void k_fill_zero(S *g, uint64_t count)
 {
     for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < count;
          i += uint64_t(gridDim.x) * blockDim.x)
-        g[i] = S(0);
+        g[i] = from_d<S>(0.0);
 }
 
 // out[i*cn + k] = f_i (absolute, or deviation) at node n0 + k
@@ -104,7 +118,43 @@ __global__ void k_scatter_f(S *g, BoxDesc b, uint64_t n0, uint64_t cn, const dou
                 for (int cz = -1; cz <= 1; ++cz) {
                     const int i = slot_of(cx, cy, cz);
                     const double w = w1(cx) * w1(cy) * w1(cz);
-                    g[uint64_t(i) * b.n + n0 + k] = S(in[uint64_t(i) * cn + k] - w * b.rho0);
+                    g[uint64_t(i) * b.n + n0 + k] = from_d<S>(in[uint64_t(i) * cn + k] - w * b.rho0);
+                }
+    }
+}
+
+// Natural-form thermal sample g_i = sqrt(rho0 kT w_i / c_s^2) xi_i.
+template <typename S>
+__global__ void k_init_thermal(S *g, BoxDesc b, double kT, uint32_t key0, uint32_t key1)
+{
+    uint32_t rk[20];
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = key0 + uint32_t(r) * 0x9E3779B9u;
+        rk[2 * r + 1] = key1 + uint32_t(r) * 0xBB67AE85u;
+    }
+    for (uint64_t n = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; n < b.n;
+         n += uint64_t(gridDim.x) * blockDim.x) {
+        double xi[28];
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+            const u32x4 o = philox4x32_10(u32x4{uint32_t(n), 0u, uint32_t(6 + j), 0u}, rk);
+            double rad, c, sn;
+            box_muller(o.x, o.y, rad, c, sn);
+            xi[4 * j] = rad * c;
+            xi[4 * j + 1] = rad * sn;
+            box_muller(o.z, o.w, rad, c, sn);
+            xi[4 * j + 2] = rad * c;
+            xi[4 * j + 3] = rad * sn;
+        }
+#pragma unroll
+        for (int cx = -1; cx <= 1; ++cx)
+#pragma unroll
+            for (int cy = -1; cy <= 1; ++cy)
+#pragma unroll
+                for (int cz = -1; cz <= 1; ++cz) {
+                    const int i = slot_of(cx, cy, cz);
+                    const double w = w1(cx) * w1(cy) * w1(cz);
+                    g[uint64_t(i) * b.n + n] = from_d<S>(sqrt(b.rho0 * kT * w * 3.0) * xi[i]);
                 }
     }
 }
@@ -289,11 +339,23 @@ inline int grid_for(uint64_t work, int block)
 
 }  // namespace
 
+// Calls f with a value of the storage type of precision code prec
+// (0 double, 1 float, 2 half).
+template <typename F>
+void with_storage(int prec, F &&f)
+{
+    if (prec == 0) f(double{});
+    else if (prec == 1) f(float{});
+    else f(__half{});
+}
+
 cudaError_t launch_fill_rest(void *g, int prec, uint64_t count, cudaStream_t s)
 {
     const int grid = grid_for(count, 256) > 4096 ? 4096 : grid_for(count, 256);
-    if (prec == 0) k_fill_zero<double><<<grid, 256, 0, s>>>(static_cast<double *>(g), count);
-    else k_fill_zero<float><<<grid, 256, 0, s>>>(static_cast<float *>(g), count);
+    with_storage(prec, [&](auto tag) {
+        using S = decltype(tag);
+        k_fill_zero<S><<<grid, 256, 0, s>>>(static_cast<S *>(g), count);
+    });
     return cudaGetLastError();
 }
 
@@ -301,8 +363,10 @@ cudaError_t launch_gather_f(const void *g, int prec, const BoxDesc &b, uint64_t 
                             double *out, bool deviations, cudaStream_t s)
 {
     const int grid = grid_for(cn, 128);
-    if (prec == 0) k_gather_f<double><<<grid, 128, 0, s>>>(static_cast<const double *>(g), b, n0, cn, out, deviations);
-    else k_gather_f<float><<<grid, 128, 0, s>>>(static_cast<const float *>(g), b, n0, cn, out, deviations);
+    with_storage(prec, [&](auto tag) {
+        using S = decltype(tag);
+        k_gather_f<S><<<grid, 128, 0, s>>>(static_cast<const S *>(g), b, n0, cn, out, deviations);
+    });
     return cudaGetLastError();
 }
 
@@ -310,10 +374,10 @@ cudaError_t launch_gather_state(const void *g, int prec, const BoxDesc &b, uint6
                                 void *out, cudaStream_t s)
 {
     const int grid = grid_for(cn, 128);
-    if (prec == 0)
-        k_gather_state<double><<<grid, 128, 0, s>>>(static_cast<const double *>(g), b, n0, cn, static_cast<double *>(out));
-    else
-        k_gather_state<float><<<grid, 128, 0, s>>>(static_cast<const float *>(g), b, n0, cn, static_cast<float *>(out));
+    with_storage(prec, [&](auto tag) {
+        using S = decltype(tag);
+        k_gather_state<S><<<grid, 128, 0, s>>>(static_cast<const S *>(g), b, n0, cn, static_cast<S *>(out));
+    });
     return cudaGetLastError();
 }
 
@@ -321,8 +385,22 @@ cudaError_t launch_scatter_f(void *g, int prec, const BoxDesc &b, uint64_t n0, u
                              const double *in, cudaStream_t s)
 {
     const int grid = grid_for(cn, 128);
-    if (prec == 0) k_scatter_f<double><<<grid, 128, 0, s>>>(static_cast<double *>(g), b, n0, cn, in);
-    else k_scatter_f<float><<<grid, 128, 0, s>>>(static_cast<float *>(g), b, n0, cn, in);
+    with_storage(prec, [&](auto tag) {
+        using S = decltype(tag);
+        k_scatter_f<S><<<grid, 128, 0, s>>>(static_cast<S *>(g), b, n0, cn, in);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_thermal(void *g, int prec, const BoxDesc &b, double kT, uint64_t seed,
+                                cudaStream_t s)
+{
+    const int grid = grid_for(b.n, 128) > 8192 ? 8192 : grid_for(b.n, 128);
+    const uint32_t k0 = uint32_t(seed & 0xffffffffu), k1 = uint32_t(seed >> 32);
+    with_storage(prec, [&](auto tag) {
+        using S = decltype(tag);
+        k_init_thermal<S><<<grid, 128, 0, s>>>(static_cast<S *>(g), b, kT, k0, k1);
+    });
     return cudaGetLastError();
 }
 
@@ -330,8 +408,10 @@ cudaError_t launch_probe(const void *g, int prec, const BoxDesc &b, const long l
                          long long count, double *out, cudaStream_t s)
 {
     const int grid = grid_for(uint64_t(count), 128);
-    if (prec == 0) k_probe<double><<<grid, 128, 0, s>>>(static_cast<const double *>(g), b, nodes, count, out);
-    else k_probe<float><<<grid, 128, 0, s>>>(static_cast<const float *>(g), b, nodes, count, out);
+    with_storage(prec, [&](auto tag) {
+        using S = decltype(tag);
+        k_probe<S><<<grid, 128, 0, s>>>(static_cast<const S *>(g), b, nodes, count, out);
+    });
     return cudaGetLastError();
 }
 
@@ -339,19 +419,23 @@ cudaError_t launch_moments(const void *g, int prec, const BoxDesc &b, uint64_t n
                            double *out, cudaStream_t s)
 {
     const int grid = grid_for(cn, 128);
-    if (prec == 0) k_moments<double><<<grid, 128, 0, s>>>(static_cast<const double *>(g), b, n0, cn, out);
-    else k_moments<float><<<grid, 128, 0, s>>>(static_cast<const float *>(g), b, n0, cn, out);
+    with_storage(prec, [&](auto tag) {
+        using S = decltype(tag);
+        k_moments<S><<<grid, 128, 0, s>>>(static_cast<const S *>(g), b, n0, cn, out);
+    });
     return cudaGetLastError();
 }
 
+// The observable field is double for FP64 storage and float otherwise.
 cudaError_t launch_observable(const void *g, int prec, const BoxDesc &b, int obs, void *field,
                               cudaStream_t s)
 {
     const int grid = grid_for(b.n, 256);
-    if (prec == 0)
-        k_observable<double, double><<<grid, 256, 0, s>>>(static_cast<const double *>(g), b, obs, static_cast<double *>(field));
-    else
-        k_observable<float, float><<<grid, 256, 0, s>>>(static_cast<const float *>(g), b, obs, static_cast<float *>(field));
+    with_storage(prec, [&](auto tag) {
+        using S = decltype(tag);
+        using F = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
+        k_observable<S, F><<<grid, 256, 0, s>>>(static_cast<const S *>(g), b, obs, static_cast<F *>(field));
+    });
     return cudaGetLastError();
 }
 

@@ -47,6 +47,7 @@ struct flbm_ctx {
     uint64_t n = 0;
     int64_t step = 0;
     int phase = 0;                 // storage is natural when ((step + phase) & 1) == 0
+    uint32_t tx_pad = 0;           // failure injection into the row pipeline (tests)
     int grid = 1;                  // persistent grid of the direct step kernel
     int row_grid = 0;              // persistent grid of the TMA row pipeline (0: unused)
     double *partials = nullptr;    // [max(grid, row_grid)][NSTAT]
@@ -93,7 +94,7 @@ int fail(flbm_ctx *c, int code, const std::string &msg)
 
 size_t elem_size(int prec) { return prec == FLBM_FP64 ? 8 : prec == FLBM_FP32 ? 4 : 2; }
 
-int prec_code(const flbm_ctx *c) { return c->p.precision == FLBM_FP64 ? 0 : 1; }
+int prec_code(const flbm_ctx *c) { return c->p.precision == FLBM_FP64 ? 0 : (c->p.precision == FLBM_FP32 ? 1 : 2); }
 
 int parity(const flbm_ctx *c) { return int((c->step + c->phase) & 1); }
 
@@ -195,6 +196,7 @@ StepArgs<R> make_args(const flbm_ctx *c, int64_t t)
     a.nchunks = uint64_t(a.cpr) * a.ny * a.nz;
     a.step = uint64_t(t);
     fill_constants_t<R>(c->p, a);
+    a.tx_pad = c->tx_pad;
     a.partials = c->partials;
     a.flag = &c->dflags->flag;
     a.bad_step = &c->dflags->bad_step;
@@ -240,8 +242,6 @@ int create_impl(const flbm_params *p, void *dev_buf, size_t dev_bytes, void *str
     *out = nullptr;
     const std::string why = validate(p);
     if (!why.empty()) return fail(nullptr, FLBM_E_INVALID, why);
-    if (p->precision == FLBM_FP16)
-        return fail(nullptr, FLBM_E_UNSUPPORTED, "FP16 storage is not built in this library");
     flbm_ctx *c = new (std::nothrow) flbm_ctx;
     if (!c) return fail(nullptr, FLBM_E_NOMEM, "host allocation failed");
     c->p = *p;
@@ -288,8 +288,10 @@ int create_impl(const flbm_params *p, void *dev_buf, size_t dev_bytes, void *str
     int occ = 1, occ_rows = 0;
     if (p->precision == FLBM_FP64)
         step_occupancy_f64(p->scheme, uint32_t(p->nx), true, occ, occ_rows);
-    else
+    else if (p->precision == FLBM_FP32)
         step_occupancy_f32(p->scheme, uint32_t(p->nx), c->n, true, occ, occ_rows);
+    else
+        step_occupancy_f16(p->scheme, uint32_t(p->nx), c->n, true, occ, occ_rows);
     const uint64_t nchunks = uint64_t((p->nx + kBlock - 1) / kBlock) * p->ny * p->nz;
     // FLBM_CTAS_PER_SM (environment) caps the direct kernel's grid below the
     // occupancy limit; a tuning knob, the default is the occupancy limit
@@ -300,6 +302,11 @@ int create_impl(const flbm_params *p, void *dev_buf, size_t dev_bytes, void *str
     }
     c->grid = int(std::min<uint64_t>(nchunks, uint64_t(c->nsm) * per_sm));
     if (c->grid < 1) c->grid = 1;
+    // FLBM_INJECT_STARVE=1 (environment, failure-injection tests only): the
+    // row pipeline expects 16 bytes more than it copies, so its bounded waits
+    // run out and flbm_step reports FLBM_E_TIMEOUT
+    if (const char *inj = std::getenv("FLBM_INJECT_STARVE"))
+        if (std::atoi(inj) == 1) c->tx_pad = 16;
     // FLBM_ROWS=0 (environment) disables the TMA row pipeline
     const char *rows_env = std::getenv("FLBM_ROWS");
     if (occ_rows > 0 && !(rows_env && std::atoi(rows_env) == 0)) {
@@ -394,9 +401,12 @@ int flbm_step(flbm_ctx *c, int64_t n)
         if (c->p.precision == FLBM_FP64)
             e = launch_step_f64(static_cast<double *>(c->g), make_args<double>(c, t), c->p.scheme, odd,
                                 stats, c->grid, c->row_grid, c->stream);
-        else
+        else if (c->p.precision == FLBM_FP32)
             e = launch_step_f32(static_cast<float *>(c->g), make_args<float>(c, t), c->p.scheme, odd,
                                 stats, c->grid, c->row_grid, c->stream);
+        else
+            e = launch_step_f16(c->g, make_args<float>(c, t), c->p.scheme, odd, stats, c->grid,
+                                c->row_grid, c->stream);
         if (e != cudaSuccess) return fail(c, FLBM_E_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
         if (c->timing) {
             CK(c, cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream));
@@ -563,6 +573,19 @@ int flbm_set_populations(flbm_ctx *c, const double *f)
     }
     c->phase = int(c->step & 1);   // natural form at the current step
     rc = reset_flags(c);
+    if (rc) return rc;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLBM_OK;
+}
+
+int flbm_init_thermal(flbm_ctx *c, uint64_t seed)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    BoxDesc b = box_of(c);
+    b.parity = 0;
+    CK(c, launch_init_thermal(c->g, prec_code(c), b, c->p.kT, seed, c->stream));
+    c->phase = int(c->step & 1);   // natural form at the current step
+    int rc = reset_flags(c);
     if (rc) return rc;
     CK(c, cudaStreamSynchronize(c->stream));
     return FLBM_OK;

@@ -35,7 +35,8 @@ struct StepArgs {
     uint64_t step;                // t of this collision (noise counter)
     uint32_t rk[20];              // Philox round keys (k0, k1) of rounds 0..9
     int32_t noise_rho0;           // phi_k uses rho0 instead of rho(x,t)
-    int32_t pad_;
+    uint32_t tx_pad;              // failure injection: bytes the row pipeline
+                                  // expects beyond what it copies (0 normally)
     R rho0;
     R sqrt_rho0;
     // Per-mode coefficients of the post-collision amplitudes in the
@@ -67,11 +68,14 @@ cudaError_t launch_step_f64(double *g, const StepArgs<double> &a, int scheme, bo
                             bool stats, int grid, int row_grid, cudaStream_t s);
 cudaError_t launch_step_f32(float *g, const StepArgs<float> &a, int scheme, bool odd,
                             bool stats, int grid, int row_grid, cudaStream_t s);
+cudaError_t launch_step_f16(void *g, const StepArgs<float> &a, int scheme, bool odd,
+                            bool stats, int grid, int row_grid, cudaStream_t s);
 // Resident CTAs per SM of the direct kernel and of the row pipeline (0 when
 // it does not serve rows of length nx) for (precision, scheme, stats); also
 // prepares the kernels' shared-memory attributes on the current device.
 void step_occupancy_f64(int scheme, uint32_t nx, bool stats, int &direct, int &rows);
 void step_occupancy_f32(int scheme, uint32_t nx, uint64_t n, bool stats, int &direct, int &rows);
+void step_occupancy_f16(int scheme, uint32_t nx, uint64_t n, bool stats, int &direct, int &rows);
 
 // Step constants shared by flbm_step and flbm_step_noalloc (capi.cu): the
 // Philox round keys, the density used by the noise, and the per-mode
@@ -81,7 +85,8 @@ void fill_step_constants(const flbm_params &p, StepArgs<double> &a);
 // Set the calling thread's error text returned by flbm_last_error(NULL).
 void set_thread_error(const char *msg);
 
-// Auxiliary kernels (aux.cu).  `prec` is 0 (double storage) or 1 (float).
+// Auxiliary kernels (aux.cu).  `prec` is 0 (double storage), 1 (float) or
+// 2 (half).
 struct BoxDesc {
     uint32_t nx, ny, nz;
     uint64_t n;
@@ -95,6 +100,8 @@ cudaError_t launch_gather_state(const void *g, int prec, const BoxDesc &b, uint6
                                 uint64_t cn, void *out, cudaStream_t s);
 cudaError_t launch_scatter_f(void *g, int prec, const BoxDesc &b, uint64_t n0, uint64_t cn,
                              const double *in, cudaStream_t s);
+cudaError_t launch_init_thermal(void *g, int prec, const BoxDesc &b, double kT, uint64_t seed,
+                                cudaStream_t s);
 cudaError_t launch_probe(const void *g, int prec, const BoxDesc &b, const long long *nodes,
                          long long count, double *out, cudaStream_t s);
 cudaError_t launch_moments(const void *g, int prec, const BoxDesc &b, uint64_t n0, uint64_t cn,

@@ -39,6 +39,8 @@
 //                a row, direct coalesced loads and stores.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include <type_traits>
 
 #include "internal.h"
@@ -60,6 +62,19 @@ template <> struct Conv<float, float> {
     static __device__ __forceinline__ float ld(const float *p) { return __ldcg(p); }
     static __device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
 };
+template <> struct Conv<__half, float> {
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldcg(p)); }
+    static __device__ __forceinline__ void st(__half *p, float v) { __stcs(p, __float2half_rn(v)); }
+};
+// Shared-memory staging element conversions of the row pipeline.
+__device__ __forceinline__ float stage_ld(const float &v) { return v; }
+__device__ __forceinline__ double stage_ld(const double &v) { return v; }
+__device__ __forceinline__ float stage_ld(const __half &v) { return __half2float(v); }
+template <typename S> __device__ __forceinline__ S stage_st(float v);
+template <> __device__ __forceinline__ float stage_st<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half stage_st<__half>(float v) { return __float2half_rn(v); }
+template <typename S> __device__ __forceinline__ S stage_st(double v);
+template <> __device__ __forceinline__ double stage_st<double>(double v) { return v; }
 
 template <typename R> __device__ __forceinline__ R rcp_(R v);
 template <> __device__ __forceinline__ double rcp_<double>(double v) { return 1.0 / v; }
@@ -357,18 +372,20 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  "r"(bytes)
                  : "memory");
 }
-// Bounded wait for the phase with the given parity: false after 2^22 polls.
+// Bounded wait for the phase with the given parity: each poll suspends for
+// at most 1 us (suspend-time hint), and the wait gives up after 2^20 polls
+// (about one second) and returns false.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {
     const uint32_t addr = smem_u32(bar);
-    for (uint32_t it = 0; it < (1u << 22); ++it) {
+    for (uint32_t it = 0; it < (1u << 20); ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n"
-            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
             " selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(addr), "r"(parity)
+            : "r"(addr), "r"(parity), "r"(1000u)
             : "memory");
         if (done) return true;
     }
@@ -440,7 +457,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 // compute warps release the stage through empty[s], bulk store back to HBM).
 // Every wait is bounded; a wait that runs out sets flag bit 1 and stops.
 template <typename S, typename R, int SCHEME, bool ODD, bool STATS>
-__global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) <= 4 ? 2 : 1)
     k_step_rows(S *__restrict__ g, const StepArgs<R> a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -494,7 +511,7 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) == 4 ? 2 : 1)
             }
             if (lane == 0) {
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&full[s], uint32_t(kQ) * seg_bytes);
+                mbar_arrive_expect_tx(&full[s], uint32_t(kQ) * seg_bytes + a.tx_pad);
             }
             __syncwarp();
             if (d < kQ)
@@ -528,7 +545,7 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) == 4 ? 2 : 1)
 #pragma unroll
                         for (int kk = 0; kk < 3; ++kk) {
                             const uint32_t pos = ODD ? xsh[2 - i] : x;
-                            v[i][j][kk] = R(st[(9 * i + 3 * j + kk) * nx + pos]);
+                            v[i][j][kk] = R(stage_ld(st[(9 * i + 3 * j + kk) * nx + pos]));
                         }
                 collide_core<R, SCHEME, STATS>(v, a, x + nx * (y + a.ny * z), acc);
                 // a8: f*_c(x) to segment d(-c) at x (even) / x + c_x (odd)
@@ -539,7 +556,7 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) == 4 ? 2 : 1)
 #pragma unroll
                         for (int kk = 0; kk < 3; ++kk) {
                             const uint32_t pos = ODD ? xsh[i] : x;
-                            st[(9 * (2 - i) + 3 * (2 - j) + (2 - kk)) * nx + pos] = S(v[i][j][kk]);
+                            st[(9 * (2 - i) + 3 * (2 - j) + (2 - kk)) * nx + pos] = stage_st<S>(v[i][j][kk]);
                         }
             }
             fence_proxy_async_smem();   // generic-proxy writes before the bulk store reads

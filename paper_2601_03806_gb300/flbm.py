@@ -73,6 +73,7 @@ def _load():
         "flbm_get_populations": ([vp, vp], i32),
         "flbm_set_populations": ([vp, vp], i32),
         "flbm_probe": ([vp, vp, i64, vp], i32),
+        "flbm_init_thermal": ([vp, u64], i32),
         "flbm_get_state": ([vp, vp], i32),
         "flbm_set_state": ([vp, vp], i32),
         "flbm_timing_enable": ([vp, i32], i32),
@@ -106,6 +107,7 @@ flbm_structure_factor = lib.flbm_structure_factor
 flbm_get_populations = lib.flbm_get_populations
 flbm_set_populations = lib.flbm_set_populations
 flbm_probe = lib.flbm_probe
+flbm_init_thermal = lib.flbm_init_thermal
 flbm_get_state = lib.flbm_get_state
 flbm_set_state = lib.flbm_set_state
 flbm_timing_enable = lib.flbm_timing_enable
@@ -242,6 +244,10 @@ class Lattice:
         ff = np.ascontiguousarray(f, np.float64).reshape(Q, self.nz, self.ny, self.nx)
         self._check(lib.flbm_set_populations(self._h, _ptr(ff)))
 
+    def init_thermal(self, seed: int) -> None:
+        """Sample the lattice invariant measure (see flbm_init_thermal)."""
+        self._check(lib.flbm_init_thermal(self._h, int(seed)))
+
     def probe(self, nodes) -> np.ndarray:
         """Absolute f_i at the listed node indices, shape (len(nodes), 27)."""
         nn = np.ascontiguousarray(nodes, np.int64)
@@ -250,7 +256,8 @@ class Lattice:
         return out
 
     def state_dtype(self):
-        return np.float64 if self.params.precision == FLBM_FP64 else np.float32
+        return {FLBM_FP64: np.float64, FLBM_FP32: np.float32, FLBM_FP16: np.float16}[
+            self.params.precision]
 
     def get_state(self, out=None) -> np.ndarray:
         if out is None:

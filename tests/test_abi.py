@@ -60,7 +60,7 @@ int main(void) {
 
 @pytest.mark.parametrize("kw,code", [
     (dict(tau=0.5), -1), (dict(tau=0.3), -1), (dict(kT=-1e-5), -1), (dict(rho0=0.0), -1),
-    (dict(nx=0), -1), (dict(scheme=7), -1), (dict(precision=2), -6), (dict(stats_every=-1), -1),
+    (dict(nx=0), -1), (dict(scheme=7), -1), (dict(precision=3), -1), (dict(stats_every=-1), -1),
     (dict(tau=float("nan")), -1),
 ])
 def test_validation_before_device(F, kw, code):

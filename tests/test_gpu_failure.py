@@ -1,0 +1,33 @@
+"""Failure detection on the GPU without a GPU fault.
+
+* Instability: a non-finite population injected from the host is reported
+  as FLBM_E_UNSTABLE (tests/test_gpu_parity.py).
+* Bounded waits: the TMA row pipeline's mbarrier waits give up after about a
+  second.  FLBM_INJECT_STARVE=1 makes a context's row pipeline expect 16
+  bytes more than it copies, so the "full" barrier never completes; the wait
+  must run out, the step must return FLBM_E_TIMEOUT, and the device must stay
+  usable for the next context.
+"""
+import time
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_row_pipeline_wait_runs_out_and_reports_timeout(monkeypatch):
+    from paper_2601_03806_gb300 import flbm
+    monkeypatch.setenv("FLBM_INJECT_STARVE", "1")
+    g = flbm.Lattice(64, 4, 3, 0.8, 1e-5, precision=flbm.FLBM_FP32)
+    monkeypatch.delenv("FLBM_INJECT_STARVE")
+    t0 = time.time()
+    with pytest.raises(flbm.FlbmError) as ei:
+        g.step(1)
+    assert ei.value.code == flbm.FLBM_E_TIMEOUT
+    assert time.time() - t0 < 30
+    g.close()
+    # the device and the library stay usable
+    h = flbm.Lattice(64, 4, 3, 0.8, 1e-5, precision=flbm.FLBM_FP32)
+    h.step(3)
+    assert abs(h.stats()["mass"] / (64 * 4 * 3) - 1) < 1e-6
