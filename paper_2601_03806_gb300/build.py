@@ -18,7 +18,7 @@ BUILD = os.path.join(ROOT, "_build")
 SOURCES = ["capi.cu", "aux.cu", "step_f32.cu", "step_f64.cu", "step_f16.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
-         "-I" + os.path.join(ROOT, "include")]
+         "-ftz=true", "-I" + os.path.join(ROOT, "include")]
 # extra nvcc flags, e.g. FLBM_NVCC_FLAGS="-DFLBM_MIN_BLOCKS=5" (register bound
 # of the step kernel); the default build uses none
 EXTRA = os.environ.get("FLBM_NVCC_FLAGS", "").split()

@@ -127,42 +127,21 @@ std::string validate(const flbm_params *p)
     return "";
 }
 
-// phi_k / sqrt(rho) of Eqs. fluct_phi (k = 4..9; all k for BGK-FLBM) and
-// fluct_phig (k = 10..26, GMF-FLBM and Reg-FLBM); c_s^2 = 1/3.
-double noise_amplitude(const flbm_params &p, int k, double bk)
-{
-    const double omega = 1.0 / p.tau;
-    const bool ghost = k >= 10;
-    const double fac = (ghost && p.scheme != FLBM_BGK) ? 1.0 : omega * (2.0 - omega);
-    return std::sqrt(p.kT * fac * bk * 3.0);
-}
-
-// Mode coefficients of Eq. flbe2 (GMF), Eq. flbe (BGK) and Reg-FLBM in the
-// kernel's scaled units: post-collision M_k = a_eq,k + lambda_k (m_k - a_eq,k)
-// + phi_k r_k, with lambda_k = 1 - omega for k = 4..9 (all non-conserved k
-// for BGK) and 0 for GMF/Reg ghosts; a_eq,k = rho u^deg for Reg ghosts, 0 for
-// BGK ghosts (second-order f^eq), absent for GMF ghosts (filtered).
+// Relaxation and noise scalars of Eq. flbe2 (GMF), Eq. flbe (BGK) and
+// Reg-FLBM: post-collision M_k = a_eq,k + lambda_k (m_k - a_eq,k) + phi_k r_k
+// with lambda_k = 1 - omega for k = 4..9 (every non-conserved k for BGK),
+// phi_k = sqrt(rho kT omega (2 - omega) b_k / c_s^2) (Eq. fluct_phi; all k for
+// BGK) and phi_k^g = sqrt(rho kT b_k / c_s^2) for the GMF / Reg ghosts (Eq.
+// fluct_phig).  The kernel multiplies amp_h / amp_g by sqrt(rho) and by the
+// compile-time sqrt(b_k / c_s^2).
 template <typename R>
 void mode_coefficients(const flbm_params &p, StepArgs<R> &a)
 {
-    const double omega = 1.0 / p.tau, lam = 1.0 - omega;
-    for (int k = 0; k < kQ; ++k) a.cq_m[k] = a.cq_eq[k] = a.ncq[k] = R(0);
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            for (int l = 0; l < 3; ++l) {
-                const int k = mode_of(i, j, l);
-                const int ord = mode_order(i, j, l);
-                if (ord < 2) continue;
-                const double syn = syn_scale(i, j, l), fwd = fwd_scale(i, j, l);
-                double lk, eq;
-                if (ord == 2) { lk = lam; eq = omega; }
-                else if (p.scheme == FLBM_BGK) { lk = lam; eq = 0.0; }
-                else if (p.scheme == FLBM_REG) { lk = 0.0; eq = 1.0; }
-                else { lk = 0.0; eq = 0.0; }
-                a.cq_m[k] = R(syn * lk / fwd);
-                a.cq_eq[k] = R(syn * eq);
-                a.ncq[k] = R(syn * noise_amplitude(p, k, b_of(i, j, l)));
-            }
+    const double omega = 1.0 / p.tau;
+    a.lambda = R(1.0 - omega);
+    a.omega = R(omega);
+    a.amp_h = R(std::sqrt(p.kT * omega * (2.0 - omega)));
+    a.amp_g = p.scheme == FLBM_BGK ? a.amp_h : R(std::sqrt(p.kT));
 }
 
 template <typename R>

@@ -39,14 +39,12 @@ struct StepArgs {
                                   // expects beyond what it copies (0 normally)
     R rho0;
     R sqrt_rho0;
-    // Per-mode coefficients of the post-collision amplitudes in the
-    // reconstruction's prescaled units (Q_k = syn_scale_k M_k):
-    //   Q_k = cq_m[k] * (fwd_scale_k m_k) + cq_eq[k] * a_eq,k + ncq[k] sqrt(rho) r_k
-    // with m_k the pre-collision Hermite moment, a_eq,k = rho u^deg(k), r_k
-    // the k-th standard normal (k >= 4).
-    R cq_m[kQ];
-    R cq_eq[kQ];
-    R ncq[kQ];
+    // Relaxation and noise scalars; the per-mode factors (syn_scale,
+    // fwd_scale, sqrt(b_k / c_s^2)) are compile-time constants of the kernel.
+    R lambda;                     // 1 - omega: k = 4..9, and every k for BGK-FLBM
+    R omega;                      // weight of the equilibrium in k = 4..9
+    R amp_h;                      // sqrt(kT omega (2 - omega)), Eq. fluct_phi
+    R amp_g;                      // ghosts: sqrt(kT) (Eq. fluct_phig), amp_h for BGK
     double *partials;             // [gridDim.x][NSTAT] when reducing
     unsigned int *flag;           // bit 0: instability; bit 1: a bounded wait ran out
     unsigned long long *bad_step; // first step that met rho <= 0 / non-finite

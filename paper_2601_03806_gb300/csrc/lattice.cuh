@@ -118,6 +118,18 @@ __host__ __device__ constexpr double fwd_scale(int a, int b, int c)
     return (a == 2 ? 3.0 : 1.0) * (b == 2 ? 3.0 : 1.0) * (c == 2 ? 3.0 : 1.0);
 }
 __host__ __device__ constexpr double kappa1d(int d) { return d == 0 ? 1.0 / 6.0 : 0.5; }
+
+// sqrt(b_k / c_s^2) of mode (a,b,c): sqrt(3) prod sqrt(beta_d), with
+// sqrt(beta) = (1, 1/sqrt(3), sqrt(2)/3) written as literals so the product
+// folds to an immediate.
+__host__ __device__ constexpr double sqrt_beta1d(int d)
+{
+    return d == 0 ? 1.0 : (d == 1 ? 0.57735026918962576451 : 0.47140452079103168293);
+}
+__host__ __device__ constexpr double sqrt_b_over_cs2(int a, int b, int c)
+{
+    return 1.7320508075688772935 * sqrt_beta1d(a) * sqrt_beta1d(b) * sqrt_beta1d(c);
+}
 __host__ __device__ constexpr double syn_scale(int a, int b, int c)
 {
     return kappa1d(a) * kappa1d(b) * kappa1d(c);

@@ -76,12 +76,14 @@ template <> __device__ __forceinline__ __half stage_st<__half>(float v) { return
 template <typename S> __device__ __forceinline__ S stage_st(double v);
 template <> __device__ __forceinline__ double stage_st<double>(double v) { return v; }
 
+// Reciprocal and square root of the density: IEEE in FP64, the hardware
+// approximations (relative error ~1e-7) in FP32.
 template <typename R> __device__ __forceinline__ R rcp_(R v);
 template <> __device__ __forceinline__ double rcp_<double>(double v) { return 1.0 / v; }
-template <> __device__ __forceinline__ float rcp_<float>(float v) { return __frcp_rn(v); }
+template <> __device__ __forceinline__ float rcp_<float>(float v) { return __fdividef(1.0f, v); }
 template <typename R> __device__ __forceinline__ R sqrt_(R v);
 template <> __device__ __forceinline__ double sqrt_<double>(double v) { return sqrt(v); }
-template <> __device__ __forceinline__ float sqrt_<float>(float v) { return sqrtf(v); }
+template <> __device__ __forceinline__ float sqrt_<float>(float v) { return v * rsqrtf(v); }
 
 // ---------------------------------------------------------------------------
 // 1-D transforms (see lattice.cuh for the scales)
@@ -197,7 +199,7 @@ __device__ __forceinline__ void collide_core(R (&v)[3][3][3], const StepArgs<R> 
     }
 
     // a3-a5: post-collision amplitudes in the reconstruction's units,
-    // Q = syn_scale * M (coefficients in StepArgs, see mode_coefficients)
+    // Q = syn_scale * M.  The pre-collision moments v carry fwd_scale.
     R qm[3][3][3];
     const R jj[3] = {jx, jy, jz};
     const R uu[3] = {ux, uy, uz};
@@ -208,12 +210,13 @@ __device__ __forceinline__ void collide_core(R (&v)[3][3][3], const StepArgs<R> 
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const int ord = mode_order(i, j, k);
-                const int mk = mode_of(i, j, k);
+                const R syn = R(syn_scale(i, j, k));
+                const R unfwd = R(1.0 / fwd_scale(i, j, k));
                 R q;
                 if (ord == 0) {
-                    q = drho * R(syn_scale(0, 0, 0));          // deviation of M_0 = rho
+                    q = drho * syn;                             // deviation of M_0 = rho
                 } else if (ord == 1) {
-                    q = v[i][j][k] * R(syn_scale(i, j, k));     // momentum, conserved
+                    q = v[i][j][k] * syn;                       // momentum, conserved
                 } else if (ord == 2 || SCHEME == 2) {
                     // Maxwell-Boltzmann coefficient rho u_x^i u_y^j u_z^k
                     // = j_first * (remaining u factors)
@@ -224,20 +227,24 @@ __device__ __forceinline__ void collide_core(R (&v)[3][3][3], const StepArgs<R> 
                     for (int ax = 0; ax < 3; ++ax)
 #pragma unroll
                         for (int e = 0; e < rest[ax]; ++e) aeq *= uu[ax];
-                    if (ord == 2) q = a.cq_m[mk] * v[i][j][k] + a.cq_eq[mk] * aeq;
-                    else q = a.cq_eq[mk] * aeq;                 // Reg ghosts
+                    if (ord == 2)   // a_eq + (1 - omega)(m - a_eq) = omega a_eq + lambda m
+                        q = syn * (a.lambda * (v[i][j][k] * unfwd) + a.omega * aeq);
+                    else            // Reg ghosts: a_eq (unit relaxation)
+                        q = syn * aeq;
                 } else if (SCHEME == 0) {
-                    q = a.cq_m[mk] * v[i][j][k];                // BGK ghosts
+                    q = (syn * unfwd) * (a.lambda * v[i][j][k]);   // BGK ghosts
                 } else {
-                    q = R(0);                                   // GMF: filtered
+                    q = R(0);                                      // GMF: filtered
                 }
                 qm[i][j][k] = q;
             }
 
-    // a6: FDT noise, M_k += phi_k r_k for k = 4..26; each pair of normals is
-    // folded in as soon as it is drawn
+    // a6: FDT noise, M_k += phi_k r_k for k = 4..26 with phi_k = sqrt(rho) amp
+    // sqrt(b_k / c_s^2); each pair of normals is folded in as soon as it is
+    // drawn (pairs never mix hydrodynamic and ghost modes)
     {
         const R sr = a.noise_rho0 ? a.sqrt_rho0 : sqrt_(rho);
+        const R sh = sr * a.amp_h, sg = sr * a.amp_g;
 #pragma unroll
         for (int blk = 0; blk < 6; ++blk) {
             const u32x4 o = philox4x32_10(
@@ -245,14 +252,17 @@ __device__ __forceinline__ void collide_core(R (&v)[3][3][3], const StepArgs<R> 
             R rad0, c0, s0, rad1, c1, s1;
             box_muller(o.x, o.y, rad0, c0, s0);
             box_muller(o.z, o.w, rad1, c1, s1);
-            const R sc0 = sr * rad0, sc1 = sr * rad1;
+            const R sc0 = (4 + 4 * blk <= 9 ? sh : sg) * rad0;
+            const R sc1 = (6 + 4 * blk <= 9 ? sh : sg) * rad1;
             const R trig[4] = {c0, s0, c1, s1};
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const int mk = 4 + 4 * blk + m;
                 if (mk < kQ) {
                     const int d = mode_deg(mk);
-                    qm[d % 3][(d / 3) % 3][d / 9] += ((m < 2 ? sc0 : sc1) * trig[m]) * a.ncq[mk];
+                    const int di = d % 3, dj = (d / 3) % 3, dk = d / 9;
+                    const R kk = R(syn_scale(di, dj, dk) * sqrt_b_over_cs2(di, dj, dk));
+                    qm[di][dj][dk] += ((m < 2 ? sc0 : sc1) * trig[m]) * kk;
                 }
             }
         }
