@@ -46,6 +46,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=512, help="cube edge (512 = the benchmark workload)")
+    ap.add_argument("--box", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
+                    help="non-cubic box (profiling runs); overrides --size")
     ap.add_argument("--precision", choices=["fp32", "fp16", "fp64"], default="fp32",
                     help="population storage (fp32 = the benchmark workload)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -175,7 +177,7 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(size: int):
+def recorded_traffic(nodes: int):
     """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
     scaled to the box size; None if the kernel changed since the capture."""
     try:
@@ -187,7 +189,7 @@ def recorded_traffic(size: int):
         if kv.get("kernel_source_hash") != kernel_source_hash():
             return None
         per_node = float(kv["dram_bytes_per_node"])
-        return per_node * size ** 3
+        return per_node * nodes
     except Exception:
         return None
 
@@ -270,16 +272,18 @@ def metric_name():
     return "MLUPS of the fused GMF-FLBM D3Q27 stream-and-collide step (HBM roofline fraction beside it)"
 
 
-def workload_config(size, ws, precision="fp32"):
+def workload_config(size, ws, precision="fp32", box=None):
     es = BYTES_PER_NODE[precision] // 54
-    return {"workload": "GMF-FLBM D3Q27 periodic %d^3, %s deviation populations AA in place, "
+    nx, ny, nz = box if box else (size, size, size)
+    shape = "%d^3" % size if nx == ny == nz else "%dx%dx%d" % (nx, ny, nz)
+    return {"workload": "GMF-FLBM D3Q27 periodic %s, %s deviation populations AA in place, "
                         "rho0=1, kT=1e-5, tau=0.6, FP64 reductions every step"
-                        % (size, precision.upper()),
-            "nx": size, "ny": size, "nz": size, "tau": WORKLOAD["tau"], "kT": WORKLOAD["kT"],
+                        % (shape, precision.upper()),
+            "nx": nx, "ny": ny, "nz": nz, "tau": WORKLOAD["tau"], "kT": WORKLOAD["kT"],
             "rho0": WORKLOAD["rho0"], "scheme": "gmf",
             "storage": "%s deviations, AA in place" % precision,
             "stats_every": 1, "l2": "inputs larger than L2 (%.1f GB state vs 129 MB L2)"
-            % (27 * es * size ** 3 / 1e9),
+            % (27 * es * nx * ny * nz / 1e9),
             "parallelism": "replicas x%d (one independent box per GPU)" % ws}
 
 
@@ -293,13 +297,14 @@ def run_ours(args, rank, local, ws):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = args.size
-    N = n ** 3
+    nx, ny, nz = args.box if args.box else (n, n, n)
+    N = nx * ny * nz
     tau, kT, rho0 = WORKLOAD["tau"], WORKLOAD["kT"], WORKLOAD["rho0"]
     seed = WORKLOAD["seed"] + rank
     stream = torch.cuda.Stream(device=dev)
     prec = {"fp32": flbm.FLBM_FP32, "fp16": flbm.FLBM_FP16, "fp64": flbm.FLBM_FP64}[args.precision]
     es = BYTES_PER_NODE[args.precision] // 54
-    lat = flbm.Lattice(n, n, n, tau, kT, rho0=rho0, seed=seed, precision=prec,
+    lat = flbm.Lattice(nx, ny, nz, tau, kT, rho0=rho0, seed=seed, precision=prec,
                        stats_every=1, torch_memory=True, stream=stream)
     lat.init_thermal(seed)           # invariant-measure start (library kernel)
     lat.step(args.warmup)
@@ -329,8 +334,8 @@ def run_ours(args, rank, local, ws):
     k_ms = kernel_ms / max(launches, 1)
     peak, peak_src = measured_hbm_peak()
     achieved = BYTES_PER_NODE[args.precision] * N / (k_ms / 1e3) / 1e9
-    traffic = recorded_traffic(n) if args.precision == "fp32" else None
-    rows_path = n % 32 == 0 and 2 * 27 * n * es <= 200 * 1024 and os.environ.get("FLBM_ROWS", "1") != "0"
+    traffic = recorded_traffic(N) if args.precision == "fp32" else None
+    rows_path = nx % 32 == 0 and 2 * 27 * nx * es <= 200 * 1024 and os.environ.get("FLBM_ROWS", "1") != "0"
     st_name = {"fp32": "float", "fp16": "__half", "fp64": "double"}[args.precision]
     kname = ("flbm::k_step_rows<%s,GMF,*,stats> (TMA row pipeline)" % st_name if rows_path
              else "flbm::k_step<%s,GMF,*,stats> (direct)" % st_name)
@@ -395,7 +400,8 @@ def run_ours(args, rank, local, ws):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "fp16": "f16 storage / f32 arithmetic", "fp64": "f64"}[args.precision],
-            "data": "synthetic", "config": workload_config(n, ws, args.precision), "roofline": roofline,
+            "data": "synthetic", "config": workload_config(n, ws, args.precision, (nx, ny, nz)),
+            "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches) + int(args.steps),
             "clocks": clk.summary(),

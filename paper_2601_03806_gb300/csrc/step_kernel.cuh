@@ -262,7 +262,7 @@ __device__ __forceinline__ void collide_core(R (&v)[3][3][3], const StepArgs<R> 
                     const int d = mode_deg(mk);
                     const int di = d % 3, dj = (d / 3) % 3, dk = d / 9;
                     const R kk = R(syn_scale(di, dj, dk) * sqrt_b_over_cs2(di, dj, dk));
-                    qm[di][dj][dk] += ((m < 2 ? sc0 : sc1) * trig[m]) * kk;
+                    qm[di][dj][dk] += ((m < 2 ? sc0 : sc1) * kk) * trig[m];
                 }
             }
         }
@@ -428,7 +428,11 @@ __device__ __forceinline__ void fence_proxy_async_smem()
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
-constexpr int kRowCompute = 256;   // max compute threads of a row CTA (8 warps)
+// max compute threads of a row CTA (build option; 256 = 8 warps)
+#ifndef FLBM_ROW_COMPUTE
+#define FLBM_ROW_COMPUTE 256
+#endif
+constexpr int kRowCompute = FLBM_ROW_COMPUTE;
 constexpr int kRowStages = 2;      // shared-memory stages (rows in flight)
 
 // Shared staging of a row CTA per stage: 27 segments of nx elements.

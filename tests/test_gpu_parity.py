@@ -310,8 +310,12 @@ def test_row_pipeline_parity(F, O, scheme, shape):
 
 
 @pytest.mark.parametrize("precision", [0, 1, 2])
-def test_row_pipeline_matches_direct_kernel(F, O, precision, monkeypatch):
-    nx, ny, nz = 64, 6, 5
+@pytest.mark.parametrize("shape", [(64, 6, 5), (512, 3, 2)])
+def test_row_pipeline_matches_direct_kernel(F, O, precision, shape, monkeypatch):
+    """Same inputs through the TMA row pipeline (including the compile-time
+    512 stride of GMF rows; FP64 512-rows fall back to the direct kernel)
+    and through the direct kernel: identical populations."""
+    nx, ny, nz = shape
     f0 = perturbed(O, nx, ny, nz, seed=4, amp=0.02)
     out = []
     for rows in ("1", "0"):
