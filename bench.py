@@ -366,16 +366,21 @@ def run_ours(args, rank, local, ws):
         barrier(ws)
         t0 = time.perf_counter()
         lat.set_state(hstate)
+        t1 = time.perf_counter()
         lat.set_step(args.warmup)
         for _ in range(args.steps):
             lat.step(1)
             lat.stats()
+        t2 = time.perf_counter()
         if with_moments:
             rc = flbm.flbm_moments(lat.handle, hrho.data_ptr(), hj.data_ptr(), hpi.data_ptr())
             if rc != 0:
                 raise RuntimeError(flbm.flbm_last_error(lat.handle))
         torch.cuda.synchronize()
-        e_ms = (time.perf_counter() - t0) * 1e3
+        t3 = time.perf_counter()
+        e_ms = (t3 - t0) * 1e3
+        e2e_split = {"upload_ms": (t1 - t0) * 1e3, "steps_ms": (t2 - t1) * 1e3,
+                     "snapshot_ms": (t3 - t2) * 1e3}
         e_max = max_over_ranks(e_ms, ws, dev)
         import ctypes
         stats_bytes = ctypes.sizeof(flbm.flbm_stats_t) + 16
@@ -383,7 +388,8 @@ def run_ours(args, rank, local, ws):
                "h2d_bytes_per_step": state_bytes // args.steps,
                "d2h_bytes_per_step": (mom_bytes if with_moments else 0) // args.steps + stats_bytes,
                "what": "flbm_set_state from pinned host + K x (flbm_step(1) + flbm_stats)"
-                       + (" + flbm_moments snapshot to pinned host" if with_moments else "")}
+                       + (" + flbm_moments snapshot to pinned host" if with_moments else ""),
+               "split": e2e_split}
         del hstate
 
     cpu = None

@@ -56,6 +56,21 @@ __device__ __forceinline__ __half from_d<__half>(double v) { return __float2half
 template <typename S>
 __device__ __forceinline__ double ldd(const S *g, uint64_t i) { return to_d(g[i]); }
 
+// Arithmetic type of the auxiliary kernels: double for FP64 storage, float
+// otherwise (the deviations are O(1e-2) and the storage is FP32 / FP16
+// anyway; FP64 arithmetic is the slow pipe on this GPU).
+template <typename S>
+using Acc = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
+
+template <typename S>
+__device__ __forceinline__ Acc<S> lda(const S *g, uint64_t i) { return Acc<S>(to_d(g[i])); }
+template <>
+__device__ __forceinline__ float lda<float>(const float *g, uint64_t i) { return g[i]; }
+template <>
+__device__ __forceinline__ float lda<__half>(const __half *g, uint64_t i) { return __half2float(g[i]); }
+
+
+
 template <typename S>
 __global__ void k_fill_zero(S *g, uint64_t count)
 {
@@ -132,13 +147,15 @@ __global__ void k_init_thermal(S *g, BoxDesc b, double kT, uint32_t key0, uint32
         rk[2 * r] = key0 + uint32_t(r) * 0x9E3779B9u;
         rk[2 * r + 1] = key1 + uint32_t(r) * 0xBB67AE85u;
     }
+    using A = Acc<S>;
+    const A base = A(sqrt(b.rho0 * kT * 3.0));   // sqrt(rho0 kT / c_s^2)
     for (uint64_t n = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; n < b.n;
          n += uint64_t(gridDim.x) * blockDim.x) {
-        double xi[28];
+        A xi[28];
 #pragma unroll
         for (int j = 0; j < 7; ++j) {
             const u32x4 o = philox4x32_10(u32x4{uint32_t(n), 0u, uint32_t(6 + j), 0u}, rk);
-            double rad, c, sn;
+            A rad, c, sn;
             box_muller(o.x, o.y, rad, c, sn);
             xi[4 * j] = rad * c;
             xi[4 * j + 1] = rad * sn;
@@ -153,8 +170,11 @@ __global__ void k_init_thermal(S *g, BoxDesc b, double kT, uint32_t key0, uint32
 #pragma unroll
                 for (int cz = -1; cz <= 1; ++cz) {
                     const int i = slot_of(cx, cy, cz);
-                    const double w = w1(cx) * w1(cy) * w1(cz);
-                    g[uint64_t(i) * b.n + n] = from_d<S>(sqrt(b.rho0 * kT * w * 3.0) * xi[i]);
+                    // sqrt(w_i) = prod sqrt(w1): sqrt(2/3), sqrt(1/6)
+                    const double sw = (cx ? 0.40824829046386302 : 0.81649658092772603) *
+                                      (cy ? 0.40824829046386302 : 0.81649658092772603) *
+                                      (cz ? 0.40824829046386302 : 0.81649658092772603);
+                    g[uint64_t(i) * b.n + n] = from_d<S>(double(base * A(sw) * xi[i]));
                 }
     }
 }
@@ -180,45 +200,46 @@ __global__ void k_probe(const S *g, BoxDesc b, const long long *nodes, long long
     }
 }
 
-// Pre-collision moments in FP64: out planes rho, jx, jy, jz, Pxx, Pyy, Pzz,
-// Pxy, Pxz, Pyz (Pi = sum f c c, including the rest part rho0 c_s^2 delta).
+// Pre-collision moments: out planes rho, jx, jy, jz, Pxx, Pyy, Pzz, Pxy, Pxz,
+// Pyz (FP64; Pi = sum f c c includes the rest part rho0 c_s^2 delta).
 template <typename S>
 __global__ void k_moments(const S *g, BoxDesc b, uint64_t n0, uint64_t cn, double *out)
 {
+    using A = Acc<S>;
     for (uint64_t k = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; k < cn;
          k += uint64_t(gridDim.x) * blockDim.x) {
         uint32_t x, y, z;
         node_xyz(n0 + k, b, x, y, z);
-        double m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        A m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
         for (int cx = -1; cx <= 1; ++cx)
 #pragma unroll
             for (int cy = -1; cy <= 1; ++cy)
 #pragma unroll
                 for (int cz = -1; cz <= 1; ++cz) {
-                    const double gv = ldd(g, storage_index(cx, cy, cz, x, y, z, b));
+                    const A gv = lda(g, storage_index(cx, cy, cz, x, y, z, b));
                     m[0] += gv;
-                    m[1] += cx * gv;
-                    m[2] += cy * gv;
-                    m[3] += cz * gv;
-                    m[4] += (cx * cx) * gv;
-                    m[5] += (cy * cy) * gv;
-                    m[6] += (cz * cz) * gv;
-                    m[7] += (cx * cy) * gv;
-                    m[8] += (cx * cz) * gv;
-                    m[9] += (cy * cz) * gv;
+                    if (cx) m[1] += cx * gv;
+                    if (cy) m[2] += cy * gv;
+                    if (cz) m[3] += cz * gv;
+                    if (cx) m[4] += gv;
+                    if (cy) m[5] += gv;
+                    if (cz) m[6] += gv;
+                    if (cx && cy) m[7] += (cx * cy) * gv;
+                    if (cx && cz) m[8] += (cx * cz) * gv;
+                    if (cy && cz) m[9] += (cy * cz) * gv;
                 }
         const double pr = b.rho0 / 3.0;   // rest-state c_s^2 rho0 on the diagonal
-        out[0 * cn + k] = b.rho0 + m[0];
-        out[1 * cn + k] = m[1];
-        out[2 * cn + k] = m[2];
-        out[3 * cn + k] = m[3];
-        out[4 * cn + k] = pr + m[4];
-        out[5 * cn + k] = pr + m[5];
-        out[6 * cn + k] = pr + m[6];
-        out[7 * cn + k] = m[7];
-        out[8 * cn + k] = m[8];
-        out[9 * cn + k] = m[9];
+        out[0 * cn + k] = b.rho0 + double(m[0]);
+        out[1 * cn + k] = double(m[1]);
+        out[2 * cn + k] = double(m[2]);
+        out[3 * cn + k] = double(m[3]);
+        out[4 * cn + k] = pr + double(m[4]);
+        out[5 * cn + k] = pr + double(m[5]);
+        out[6 * cn + k] = pr + double(m[6]);
+        out[7 * cn + k] = double(m[7]);
+        out[8 * cn + k] = double(m[8]);
+        out[9 * cn + k] = double(m[9]);
     }
 }
 
@@ -227,20 +248,21 @@ __global__ void k_moments(const S *g, BoxDesc b, uint64_t n0, uint64_t cn, doubl
 template <typename S, typename F>
 __global__ void k_observable(const S *g, BoxDesc b, int obs, F *field)
 {
+    using A = Acc<S>;
     for (uint64_t n = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; n < b.n;
          n += uint64_t(gridDim.x) * blockDim.x) {
         uint32_t x, y, z;
         node_xyz(n, b, x, y, z);
-        double acc = 0.0;
+        A acc = 0;
 #pragma unroll
         for (int cx = -1; cx <= 1; ++cx)
 #pragma unroll
             for (int cy = -1; cy <= 1; ++cy)
 #pragma unroll
                 for (int cz = -1; cz <= 1; ++cz) {
-                    double c;
+                    int c;
                     switch (obs) {
-                    case 0: c = 1.0; break;
+                    case 0: c = 1; break;
                     case 1: c = cx + cy + cz; break;
                     case 2: c = cx * cx + cy * cy + cz * cz; break;
                     case 3: c = cx * cy + cx * cz + cy * cz; break;
@@ -248,7 +270,7 @@ __global__ void k_observable(const S *g, BoxDesc b, int obs, F *field)
                     case 5: c = cy; break;
                     default: c = cz; break;
                     }
-                    if (c != 0.0) acc += c * ldd(g, storage_index(cx, cy, cz, x, y, z, b));
+                    if (c != 0) acc += A(c) * lda(g, storage_index(cx, cy, cz, x, y, z, b));
                 }
         field[n] = F(acc);
     }

@@ -31,7 +31,7 @@ struct DevFlags {
     unsigned long long bad_step;
 };
 
-constexpr uint64_t kStageNodes = 1ull << 18;   // nodes per host-transfer chunk
+constexpr uint64_t kChunkNodes = 1ull << 20;   // nodes per host-transfer chunk
 
 }  // namespace
 
@@ -53,7 +53,13 @@ struct flbm_ctx {
     double *partials = nullptr;    // [max(grid, row_grid)][NSTAT]
     DevStats *dstats = nullptr;
     DevFlags *dflags = nullptr;
-    double *stage = nullptr;       // host-transfer staging, kStageNodes * 27 doubles
+    // host transfers: two staging buffers of pipe_nodes * 27 doubles, a copy
+    // stream, and events that hand each buffer between the streams
+    double *pipe[2] = {nullptr, nullptr};
+    uint64_t pipe_nodes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_ready[2] = {nullptr, nullptr};
+    cudaEvent_t ev_free[2] = {nullptr, nullptr};
     // S(k)
     cufftHandle plan = 0;
     bool has_plan = false;
@@ -189,10 +195,64 @@ int reset_flags(flbm_ctx *c)
     return FLBM_OK;
 }
 
-int ensure_stage(flbm_ctx *c)
+int ensure_pipe(flbm_ctx *c)
 {
-    if (c->stage) return FLBM_OK;
-    CK(c, cudaMalloc(&c->stage, kStageNodes * kQ * sizeof(double)));
+    if (c->pipe[0]) return FLBM_OK;
+    c->pipe_nodes = std::min<uint64_t>(c->n, kChunkNodes);
+    for (int b = 0; b < 2; ++b) {
+        CK(c, cudaMalloc(&c->pipe[b], c->pipe_nodes * kQ * sizeof(double)));
+        CK(c, cudaEventCreateWithFlags(&c->ev_ready[b], cudaEventDisableTiming));
+        CK(c, cudaEventCreateWithFlags(&c->ev_free[b], cudaEventDisableTiming));
+    }
+    CK(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    return FLBM_OK;
+}
+
+// Device -> host in chunks of pipe_nodes: produce(buf, n0, cn) fills a
+// staging buffer on the context stream, copy(buf, n0, cn) drains it on the
+// copy stream; chunk k + 1 is produced while chunk k is copied.
+template <typename Produce, typename Copy>
+int d2h_chunks(flbm_ctx *c, Produce produce, Copy copy)
+{
+    int rc = ensure_pipe(c);
+    if (rc) return rc;
+    int k = 0;
+    for (uint64_t n0 = 0; n0 < c->n; n0 += c->pipe_nodes, ++k) {
+        const int b = k & 1;
+        const uint64_t cn = std::min<uint64_t>(c->pipe_nodes, c->n - n0);
+        if (k >= 2) CK(c, cudaStreamWaitEvent(c->stream, c->ev_free[b], 0));
+        CK(c, produce(c->pipe[b], n0, cn));
+        CK(c, cudaEventRecord(c->ev_ready[b], c->stream));
+        CK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_ready[b], 0));
+        CK(c, copy(c->pipe[b], n0, cn));
+        CK(c, cudaEventRecord(c->ev_free[b], c->copy_stream));
+    }
+    CK(c, cudaStreamSynchronize(c->copy_stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLBM_OK;
+}
+
+// Host -> device in chunks: copy(buf, n0, cn) fills a staging buffer on the
+// copy stream, consume(buf, n0, cn) scatters it on the context stream.
+template <typename Copy, typename Consume>
+int h2d_chunks(flbm_ctx *c, Copy copy, Consume consume)
+{
+    int rc = ensure_pipe(c);
+    if (rc) return rc;
+    CK(c, cudaEventRecord(c->ev_ready[0], c->stream));   // order after earlier work
+    CK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_ready[0], 0));
+    int k = 0;
+    for (uint64_t n0 = 0; n0 < c->n; n0 += c->pipe_nodes, ++k) {
+        const int b = k & 1;
+        const uint64_t cn = std::min<uint64_t>(c->pipe_nodes, c->n - n0);
+        if (k >= 2) CK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_free[b], 0));
+        CK(c, copy(c->pipe[b], n0, cn));
+        CK(c, cudaEventRecord(c->ev_ready[b], c->copy_stream));
+        CK(c, cudaStreamWaitEvent(c->stream, c->ev_ready[b], 0));
+        CK(c, consume(c->pipe[b], n0, cn));
+        CK(c, cudaEventRecord(c->ev_free[b], c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
     return FLBM_OK;
 }
 
@@ -205,7 +265,13 @@ void release(flbm_ctx *c)
     cudaFree(c->fft_out);
     cudaFree(c->shell_s);
     cudaFree(c->shell_c);
-    cudaFree(c->stage);
+    if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(c->pipe[b]);
+        if (c->ev_ready[b]) cudaEventDestroy(c->ev_ready[b]);
+        if (c->ev_free[b]) cudaEventDestroy(c->ev_free[b]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     cudaFree(c->partials);
     cudaFree(c->dstats);
     cudaFree(c->dflags);
@@ -414,22 +480,23 @@ int flbm_step(flbm_ctx *c, int64_t n)
 int flbm_moments(flbm_ctx *c, double *rho, double *j, double *pi)
 {
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
-    int rc = ensure_stage(c);
-    if (rc) return rc;
     const BoxDesc b = box_of(c);
     const uint64_t N = c->n;
-    for (uint64_t n0 = 0; n0 < N; n0 += kStageNodes) {
-        const uint64_t cn = std::min<uint64_t>(kStageNodes, N - n0);
-        CK(c, launch_moments(c->g, prec_code(c), b, n0, cn, c->stage, c->stream));
-        const size_t w = cn * sizeof(double);
-        if (rho) CK(c, cudaMemcpyAsync(rho + n0, c->stage, w, cudaMemcpyDeviceToHost, c->stream));
-        if (j) CK(c, cudaMemcpy2DAsync(j + n0, N * sizeof(double), c->stage + cn, w, w, 3,
-                                       cudaMemcpyDeviceToHost, c->stream));
-        if (pi) CK(c, cudaMemcpy2DAsync(pi + n0, N * sizeof(double), c->stage + 4 * cn, w, w, 6,
-                                        cudaMemcpyDeviceToHost, c->stream));
-    }
-    CK(c, cudaStreamSynchronize(c->stream));
-    return FLBM_OK;
+    const int prec = prec_code(c);
+    return d2h_chunks(
+        c, [&](double *buf, uint64_t n0, uint64_t cn) { return launch_moments(c->g, prec, b, n0, cn, buf, c->stream); },
+        [&](double *buf, uint64_t n0, uint64_t cn) {
+            const size_t w = cn * sizeof(double);
+            cudaError_t e = cudaSuccess;
+            if (rho) e = cudaMemcpyAsync(rho + n0, buf, w, cudaMemcpyDeviceToHost, c->copy_stream);
+            if (e == cudaSuccess && j)
+                e = cudaMemcpy2DAsync(j + n0, N * sizeof(double), buf + cn, w, w, 3, cudaMemcpyDeviceToHost,
+                                      c->copy_stream);
+            if (e == cudaSuccess && pi)
+                e = cudaMemcpy2DAsync(pi + n0, N * sizeof(double), buf + 4 * cn, w, w, 6,
+                                      cudaMemcpyDeviceToHost, c->copy_stream);
+            return e;
+        });
 }
 
 int flbm_stats(flbm_ctx *c, flbm_stats_t *out)
@@ -519,37 +586,38 @@ int flbm_get_populations(flbm_ctx *c, double *f)
 {
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
     if (!f) return fail(c, FLBM_E_INVALID, "f is NULL");
-    int rc = ensure_stage(c);
-    if (rc) return rc;
     const BoxDesc b = box_of(c);
     const uint64_t N = c->n;
-    for (uint64_t n0 = 0; n0 < N; n0 += kStageNodes) {
-        const uint64_t cn = std::min<uint64_t>(kStageNodes, N - n0);
-        CK(c, launch_gather_f(c->g, prec_code(c), b, n0, cn, c->stage, false, c->stream));
-        const size_t w = cn * sizeof(double);
-        CK(c, cudaMemcpy2DAsync(f + n0, N * sizeof(double), c->stage, w, w, kQ,
-                                cudaMemcpyDeviceToHost, c->stream));
-    }
-    CK(c, cudaStreamSynchronize(c->stream));
-    return FLBM_OK;
+    const int prec = prec_code(c);
+    return d2h_chunks(
+        c, [&](double *buf, uint64_t n0, uint64_t cn) {
+            return launch_gather_f(c->g, prec, b, n0, cn, buf, false, c->stream);
+        },
+        [&](double *buf, uint64_t n0, uint64_t cn) {
+            const size_t w = cn * sizeof(double);
+            return cudaMemcpy2DAsync(f + n0, N * sizeof(double), buf, w, w, kQ, cudaMemcpyDeviceToHost,
+                                     c->copy_stream);
+        });
 }
 
 int flbm_set_populations(flbm_ctx *c, const double *f)
 {
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
     if (!f) return fail(c, FLBM_E_INVALID, "f is NULL");
-    int rc = ensure_stage(c);
-    if (rc) return rc;
     BoxDesc b = box_of(c);
     b.parity = 0;
     const uint64_t N = c->n;
-    for (uint64_t n0 = 0; n0 < N; n0 += kStageNodes) {
-        const uint64_t cn = std::min<uint64_t>(kStageNodes, N - n0);
-        const size_t w = cn * sizeof(double);
-        CK(c, cudaMemcpy2DAsync(c->stage, w, f + n0, N * sizeof(double), w, kQ,
-                                cudaMemcpyHostToDevice, c->stream));
-        CK(c, launch_scatter_f(c->g, prec_code(c), b, n0, cn, c->stage, c->stream));
-    }
+    const int prec = prec_code(c);
+    int rc = h2d_chunks(
+        c, [&](double *buf, uint64_t n0, uint64_t cn) {
+            const size_t w = cn * sizeof(double);
+            return cudaMemcpy2DAsync(buf, w, f + n0, N * sizeof(double), w, kQ, cudaMemcpyHostToDevice,
+                                     c->copy_stream);
+        },
+        [&](double *buf, uint64_t n0, uint64_t cn) {
+            return launch_scatter_f(c->g, prec, b, n0, cn, buf, c->stream);
+        });
+    if (rc) return rc;
     c->phase = int(c->step & 1);   // natural form at the current step
     rc = reset_flags(c);
     if (rc) return rc;
@@ -577,15 +645,15 @@ int flbm_probe(flbm_ctx *c, const int64_t *nodes, int64_t count, double *f)
     for (int64_t k = 0; k < count; ++k)
         if (nodes[k] < 0 || uint64_t(nodes[k]) >= c->n)
             return fail(c, FLBM_E_INVALID, "probe node index out of range");
-    int rc = ensure_stage(c);
+    int rc = ensure_pipe(c);
     if (rc) return rc;
     const BoxDesc b = box_of(c);
-    // staging holds kStageNodes*27 doubles: node list + 27 outputs per node
-    const int64_t chunk = int64_t(kStageNodes * kQ / (kQ + 1));
-    long long *dn = reinterpret_cast<long long *>(c->stage);
+    // a staging buffer holds pipe_nodes * 27 doubles: node list + 27 outputs per node
+    const int64_t chunk = int64_t(c->pipe_nodes * kQ / (kQ + 1));
+    long long *dn = reinterpret_cast<long long *>(c->pipe[0]);
     for (int64_t k0 = 0; k0 < count; k0 += chunk) {
         const int64_t cn = std::min<int64_t>(chunk, count - k0);
-        double *dout = c->stage + chunk;
+        double *dout = c->pipe[0] + chunk;
         CK(c, cudaMemcpyAsync(dn, nodes + k0, cn * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
         CK(c, launch_probe(c->g, prec_code(c), b, dn, cn, dout, c->stream));
         CK(c, cudaMemcpyAsync(f + k0 * kQ, dout, cn * kQ * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -602,16 +670,17 @@ int flbm_get_state(flbm_ctx *c, void *host)
     if (parity(c) == 0) {
         CK(c, cudaMemcpyAsync(host, c->g, c->g_bytes, cudaMemcpyDeviceToHost, c->stream));
     } else {
-        int rc = ensure_stage(c);
-        if (rc) return rc;
         const BoxDesc b = box_of(c);
         const uint64_t N = c->n;
-        for (uint64_t n0 = 0; n0 < N; n0 += kStageNodes) {
-            const uint64_t cn = std::min<uint64_t>(kStageNodes, N - n0);
-            CK(c, launch_gather_state(c->g, prec_code(c), b, n0, cn, c->stage, c->stream));
-            CK(c, cudaMemcpy2DAsync(static_cast<char *>(host) + n0 * es, N * es, c->stage, cn * es,
-                                    cn * es, kQ, cudaMemcpyDeviceToHost, c->stream));
-        }
+        const int prec = prec_code(c);
+        return d2h_chunks(
+            c, [&](double *buf, uint64_t n0, uint64_t cn) {
+                return launch_gather_state(c->g, prec, b, n0, cn, buf, c->stream);
+            },
+            [&](double *buf, uint64_t n0, uint64_t cn) {
+                return cudaMemcpy2DAsync(static_cast<char *>(host) + n0 * es, N * es, buf, cn * es, cn * es,
+                                         kQ, cudaMemcpyDeviceToHost, c->copy_stream);
+            });
     }
     CK(c, cudaStreamSynchronize(c->stream));
     return FLBM_OK;
