@@ -15,7 +15,7 @@ constexpr int kBlock = 128;   // threads per CTA of the step kernel (one x-row c
 // Minimum resident CTAs per SM requested from the compiler for the step
 // kernel (bounds its registers per thread); a build option.
 #ifndef FLBM_MIN_BLOCKS
-#define FLBM_MIN_BLOCKS 5
+#define FLBM_MIN_BLOCKS 4
 #endif
 // Slots of the fused FP64 reductions (row a9).  Sums over nodes of the
 // pre-collision state: drho = rho - rho0, j, u^2 and the four

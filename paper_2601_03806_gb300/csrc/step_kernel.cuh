@@ -147,12 +147,48 @@ __device__ __forceinline__ void block_reduce_store(const R (&acc)[NSTAT], double
 }
 
 // ---------------------------------------------------------------------------
+// a6, first half: the node's 23 standard normals r_k (k = 4..26), drawn from
+// Philox4x32-10 keyed on (seed; node, step, block) + Box-Muller and scaled by
+// the compile-time syn_scale_k sqrt(b_k / c_s^2): nz[k - 4].  They depend
+// only on (node, step), so the kernels draw them while the populations are
+// still in flight.
+
+constexpr int kNoise = kQ - 4;
+
+template <typename R>
+__device__ __forceinline__ void draw_noise(const StepArgs<R> &a, uint32_t node, R (&nz)[kNoise])
+{
+#pragma unroll
+    for (int blk = 0; blk < 6; ++blk) {
+        const u32x4 o = philox4x32_10(
+            u32x4{node, uint32_t(a.step), uint32_t(blk), uint32_t(a.step >> 32)}, a.rk);
+        R rad0, c0, s0, rad1, c1, s1;
+        box_muller(o.x, o.y, rad0, c0, s0);
+        box_muller(o.z, o.w, rad1, c1, s1);
+        const R trig[4] = {c0, s0, c1, s1};
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int mk = 4 + 4 * blk + m;
+            if (mk < kQ) {
+                const int d = mode_deg(mk);
+                const int di = d % 3, dj = (d / 3) % 3, dk = d / 9;
+                const R kk = R(syn_scale(di, dj, dk) * sqrt_b_over_cs2(di, dj, dk));
+                nz[mk - 4] = ((m < 2 ? rad0 : rad1) * kk) * trig[m];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // a2-a7, a9: collision of one node.  v[cx+1][cy+1][cz+1] holds the incoming
 // deviations on entry and the post-collision deviations on exit.
+// PREDRAWN: nz holds the node's scaled normals (draw_noise, drawn before the
+// populations arrived); otherwise the normals of `node` are drawn here pair
+// by pair and folded in at once (fewer live registers).
 
-template <typename R, int SCHEME, bool STATS>
-__device__ __forceinline__ void collide_core(R (&v)[3][3][3], const StepArgs<R> &a, uint32_t node,
-                                             R (&acc)[NSTAT])
+template <typename R, int SCHEME, bool STATS, bool PREDRAWN>
+__device__ __forceinline__ void collide_core(R (&v)[3][3][3], const StepArgs<R> &a,
+                                             const R (&nz)[kNoise], uint32_t node, R (&acc)[NSTAT])
 {
     // a2: forward Hermite projection, three 1-D passes
 #pragma unroll
@@ -239,30 +275,38 @@ __device__ __forceinline__ void collide_core(R (&v)[3][3][3], const StepArgs<R> 
                 qm[i][j][k] = q;
             }
 
-    // a6: FDT noise, M_k += phi_k r_k for k = 4..26 with phi_k = sqrt(rho) amp
-    // sqrt(b_k / c_s^2); each pair of normals is folded in as soon as it is
-    // drawn (pairs never mix hydrodynamic and ghost modes)
+    // a6: M_k += phi_k r_k for k = 4..26 with phi_k = sqrt(rho) amp
+    // sqrt(b_k / c_s^2) (amp_h for k = 4..9, amp_g for the ghosts)
     {
         const R sr = a.noise_rho0 ? a.sqrt_rho0 : sqrt_(rho);
         const R sh = sr * a.amp_h, sg = sr * a.amp_g;
+        if (PREDRAWN) {
 #pragma unroll
-        for (int blk = 0; blk < 6; ++blk) {
-            const u32x4 o = philox4x32_10(
-                u32x4{node, uint32_t(a.step), uint32_t(blk), uint32_t(a.step >> 32)}, a.rk);
-            R rad0, c0, s0, rad1, c1, s1;
-            box_muller(o.x, o.y, rad0, c0, s0);
-            box_muller(o.z, o.w, rad1, c1, s1);
-            const R sc0 = (4 + 4 * blk <= 9 ? sh : sg) * rad0;
-            const R sc1 = (6 + 4 * blk <= 9 ? sh : sg) * rad1;
-            const R trig[4] = {c0, s0, c1, s1};
+            for (int mk = 4; mk < kQ; ++mk) {
+                const int d = mode_deg(mk);
+                qm[d % 3][(d / 3) % 3][d / 9] += (mk <= 9 ? sh : sg) * nz[mk - 4];
+            }
+        } else {
+            // pairs never mix hydrodynamic and ghost modes
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const int mk = 4 + 4 * blk + m;
-                if (mk < kQ) {
-                    const int d = mode_deg(mk);
-                    const int di = d % 3, dj = (d / 3) % 3, dk = d / 9;
-                    const R kk = R(syn_scale(di, dj, dk) * sqrt_b_over_cs2(di, dj, dk));
-                    qm[di][dj][dk] += ((m < 2 ? sc0 : sc1) * kk) * trig[m];
+            for (int blk = 0; blk < 6; ++blk) {
+                const u32x4 o = philox4x32_10(
+                    u32x4{node, uint32_t(a.step), uint32_t(blk), uint32_t(a.step >> 32)}, a.rk);
+                R rad0, c0, s0, rad1, c1, s1;
+                box_muller(o.x, o.y, rad0, c0, s0);
+                box_muller(o.z, o.w, rad1, c1, s1);
+                const R trig[4] = {c0, s0, c1, s1};
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int mk = 4 + 4 * blk + m;
+                    if (mk < kQ) {
+                        const int d = mode_deg(mk);
+                        const int di = d % 3, dj = (d / 3) % 3, dk = d / 9;
+                        const R kk = R(syn_scale(di, dj, dk) * sqrt_b_over_cs2(di, dj, dk));
+                        // same rounding order as draw_noise + the PREDRAWN branch
+                        const R t = ((m < 2 ? rad0 : rad1) * kk) * trig[m];
+                        qm[di][dj][dk] += (mk <= 9 ? sh : sg) * t;
+                    }
                 }
             }
         }
@@ -344,7 +388,8 @@ __global__ void __launch_bounds__(kBlock, FLBM_MIN_BLOCKS) k_step(S *__restrict_
                     else idx = I(slot_of(1 - i, 1 - j, 1 - k)) * N + (nb.xs[2 - i] + nb.ry[2 - j] + nb.rz[2 - k]);
                     v[i][j][k] = Conv<S, R>::ld(g + idx);
                 }
-        collide_core<R, SCHEME, STATS>(v, a, uint32_t(n), acc);
+        R nz[kNoise];   // unused: the direct kernel draws the normals inside
+        collide_core<R, SCHEME, STATS, false>(v, a, nz, uint32_t(n), acc);
         // a8: AA store
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -542,13 +587,18 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) <= 4 ? 2 : 1)
             const uint64_t row = blockIdx.x + k * gridDim.x;
             if (row >= nrows) break;
             const int s = int(k % kRowStages);
+            const uint32_t y = uint32_t(row % a.ny), z = uint32_t(row / a.ny);
+            const uint32_t rowbase = nx * (y + a.ny * z);
+            // the first node's normals are drawn while the row's segments land
+            R nz[kNoise];
+            if (threadIdx.x < nx) draw_noise(a, rowbase + threadIdx.x, nz);
             if (!mbar_wait(&full[s], uint32_t((k / kRowStages) & 1))) {
                 if (lane == 0) atomicOr(a.flag, 2u);
                 break;
             }
-            const uint32_t y = uint32_t(row % a.ny), z = uint32_t(row / a.ny);
             S *st = stage + size_t(s) * stage_elems;
             for (uint32_t x = threadIdx.x; x < nx; x += nc) {
+                if (x != threadIdx.x) draw_noise(a, rowbase + x, nz);
                 const uint32_t xsh[3] = {x ? x - 1 : nx - 1, x, (x + 1 < nx) ? x + 1 : 0};
                 // a1: incoming f_c(x) from segment d(c) at x (even) / x - c_x (odd)
                 R v[3][3][3];
@@ -561,7 +611,7 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) <= 4 ? 2 : 1)
                             const uint32_t pos = ODD ? xsh[2 - i] : x;
                             v[i][j][kk] = R(stage_ld(st[(9 * i + 3 * j + kk) * nx + pos]));
                         }
-                collide_core<R, SCHEME, STATS>(v, a, x + nx * (y + a.ny * z), acc);
+                collide_core<R, SCHEME, STATS, true>(v, a, nz, rowbase + x, acc);
                 // a8: f*_c(x) to segment d(-c) at x (even) / x + c_x (odd)
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
