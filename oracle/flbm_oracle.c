@@ -207,13 +207,15 @@ static double uniform23(uint32_t x)
     return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
-void oracle_normals(uint64_t seed, uint64_t node, uint64_t step, double r[27])
+void oracle_normals_stream(uint64_t seed, uint32_t stream, uint64_t node, uint64_t step,
+                           double r[27])
 {
     const double two_pi = 2.0 * 3.14159265358979323846;
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     for (int k = 0; k < 4; ++k) r[k] = 0.0;
     for (uint32_t j = 0; j < 6; ++j) {
-        uint32_t ctr[4] = {(uint32_t)node, (uint32_t)(step & 0xffffffffu), j,
+        /* counter word 2: block j in the low 8 bits, noise stream above */
+        uint32_t ctr[4] = {(uint32_t)node, (uint32_t)(step & 0xffffffffu), j | (stream << 8),
                            (uint32_t)(step >> 32)};
         uint32_t o[4];
         oracle_philox4x32_10(ctr, key, o);
@@ -226,6 +228,11 @@ void oracle_normals(uint64_t seed, uint64_t node, uint64_t step, double r[27])
             if (k + 1 < Q) r[k + 1] = rad * sin(two_pi * u2); /* mode 27 dropped */
         }
     }
+}
+
+void oracle_normals(uint64_t seed, uint64_t node, uint64_t step, double r[27])
+{
+    oracle_normals_stream(seed, 0u, node, step, r);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -272,7 +279,7 @@ void oracle_noise_term(int scheme, double tau, double kT, double rho,
 }
 
 static void collide(int scheme, double tau, double kT, double rho_phi0, int noise_rho0,
-                    uint64_t seed, uint64_t node, uint64_t step,
+                    uint64_t seed, uint32_t stream, uint64_t node, uint64_t step,
                     const double *f, double *fstar)
 {
     const double omega = 1.0 / tau;
@@ -284,7 +291,7 @@ static void collide(int scheme, double tau, double kT, double rho_phi0, int nois
     for (int a = 0; a < 3; ++a) u[a] = j[a] / rho;
 
     double r[Q], xi[Q];
-    oracle_normals(seed, node, step, r);
+    oracle_normals_stream(seed, stream, node, step, r);
     /* reading: phi_k uses the local density rho(x,t) (rho0 on request) */
     oracle_noise_term(scheme, tau, kT, noise_rho0 ? rho_phi0 : rho, r, xi);
 
@@ -349,7 +356,7 @@ void oracle_collide_node(int scheme, double tau, double kT, double rho_phi0,
                          uint64_t step, const double f[27], double fstar[27])
 {
     build_tables();
-    collide(scheme, tau, kT, rho_phi0, noise_rho0, seed, node, step, f, fstar);
+    collide(scheme, tau, kT, rho_phi0, noise_rho0, seed, 0u, node, step, f, fstar);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -361,6 +368,7 @@ struct oracle_box {
     double tau, kT, rho0;
     uint64_t seed;
     int scheme, noise_rho0;
+    uint32_t stream;
     int64_t step;
     double *f, *fn;
 };
@@ -416,6 +424,7 @@ void oracle_get_populations(const oracle_box *b, double *f)
 }
 
 int64_t oracle_get_step(const oracle_box *b) { return b->step; }
+void oracle_set_stream(oracle_box *b, uint32_t stream) { b->stream = stream; }
 void oracle_set_step(oracle_box *b, int64_t step) { b->step = step; }
 
 static void one_step(oracle_box *b)
@@ -432,7 +441,7 @@ static void one_step(oracle_box *b)
             for (int x = 0; x < nx; ++x) {
                 long long node = x + (long long)nx * (y + (long long)ny * z);
                 for (int i = 0; i < Q; ++i) f[i] = b->f[i * N + node];
-                collide(b->scheme, b->tau, b->kT, b->rho0, b->noise_rho0, b->seed,
+                collide(b->scheme, b->tau, b->kT, b->rho0, b->noise_rho0, b->seed, b->stream,
                         (uint64_t)node, (uint64_t)b->step, f, fs);
                 for (int i = 0; i < Q; ++i) {
                     int xd = ((x + VEL[i][0]) % nx + nx) % nx;

@@ -47,6 +47,11 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
  * key = (seed lo, seed hi); block j word m feeds mode 4+4j+m; Box-Muller on
  * consecutive word pairs; uniform u = ((x >> 9) + 0.5) * 2^-23. */
 void oracle_normals(uint64_t seed, uint64_t node, uint64_t step, double r[27]);
+/* Same with a noise stream id in the high 24 bits of counter word 2 (block
+ * j in the low 8 bits): independent streams under one seed; stream 0 is
+ * oracle_normals. */
+void oracle_normals_stream(uint64_t seed, uint32_t stream, uint64_t node, uint64_t step,
+                           double r[27]);
 
 /* Second-order equilibrium f^eq_i(rho, u). */
 void oracle_feq2(double rho, const double u[3], double feq[27]);
@@ -69,6 +74,8 @@ void oracle_set_populations(oracle_box *b, const double *f);
 void oracle_get_populations(const oracle_box *b, double *f);
 int64_t oracle_get_step(const oracle_box *b);
 void oracle_set_step(oracle_box *b, int64_t step);
+/* Noise stream id of the box (default 0); see oracle_normals_stream. */
+void oracle_set_stream(oracle_box *b, uint32_t stream);
 void oracle_step(oracle_box *b, int64_t n);
 
 /* Advance n steps, recording the populations of node 0 before every step

@@ -45,6 +45,8 @@ def lib():
         L.oracle_tables.argtypes = [vp, vp, vp, vp, vp, vp]
         L.oracle_philox4x32_10.argtypes = [vp, vp, vp]
         L.oracle_normals.argtypes = [u64, u64, u64, vp]
+        L.oracle_normals_stream.argtypes = [u64, C.c_uint32, u64, u64, vp]
+        L.oracle_set_stream.argtypes = [vp, C.c_uint32]
         L.oracle_feq2.argtypes = [d, vp, vp]
         L.oracle_noise_term.argtypes = [i32, d, d, d, vp, vp]
         L.oracle_collide_node.argtypes = [i32, d, d, d, i32, u64, u64, u64, vp, vp]
@@ -91,9 +93,9 @@ def philox4x32_10(ctr, key):
     return o
 
 
-def normals(seed: int, node: int, step: int) -> np.ndarray:
+def normals(seed: int, node: int, step: int, stream: int = 0) -> np.ndarray:
     r = np.zeros(Q)
-    lib().oracle_normals(seed, node, step, _p(r))
+    lib().oracle_normals_stream(seed, stream, node, step, _p(r))
     return r
 
 
@@ -140,7 +142,8 @@ def structure_factor(m: np.ndarray, nshell: int):
 class Box:
     """A periodic nx*ny*nz box advanced by the oracle (two arrays, push)."""
 
-    def __init__(self, nx, ny, nz, tau, kT, rho0=1.0, seed=0, scheme=GMF, noise_rho0=False):
+    def __init__(self, nx, ny, nz, tau, kT, rho0=1.0, seed=0, scheme=GMF, noise_rho0=False,
+                 stream=0):
         self.shape = (nz, ny, nx)
         self.n = nx * ny * nz
         self.nx, self.ny, self.nz = nx, ny, nz
@@ -149,6 +152,8 @@ class Box:
         if not h:
             raise ValueError("oracle_create failed")
         self._h = C.c_void_p(h)
+        if stream:
+            lib().oracle_set_stream(self._h, int(stream))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -105,15 +105,17 @@ def test_philox_known_answers(oracle_mod):
         assert [int(x) for x in out] == v[6:10]
 
 
-def test_normals_box_muller_mapping(oracle_mod):
+@pytest.mark.parametrize("stream", [0, 5, (1 << 24) - 1])
+def test_normals_box_muller_mapping(oracle_mod, stream):
     """r_k^2 + r_{k+1}^2 = -2 ln u1 of the matching Philox word pair (block j
-    word m feeds mode 4+4j+m), and r_27 is dropped."""
+    word m feeds mode 4+4j+m, counter word 2 = j | stream << 8), and r_27 is
+    dropped."""
     seed, node, step = 0x1234_5678_9ABC, 77, (1 << 33) + 5
-    r = oracle_mod.normals(seed, node, step)
+    r = oracle_mod.normals(seed, node, step, stream)
     assert np.all(r[:4] == 0)
     key = [seed & 0xFFFFFFFF, seed >> 32]
     for j in range(6):
-        o = oracle_mod.philox4x32_10([node, step & 0xFFFFFFFF, j, step >> 32], key)
+        o = oracle_mod.philox4x32_10([node, step & 0xFFFFFFFF, j | (stream << 8), step >> 32], key)
         for p in range(2):
             k = 4 + 4 * j + 2 * p
             u1 = ((int(o[2 * p]) >> 9) + 0.5) / 2 ** 23
@@ -124,6 +126,17 @@ def test_normals_box_muller_mapping(oracle_mod):
                 assert abs(np.arctan2(r[k + 1], r[k]) % (2 * np.pi) - 2 * np.pi * u2) < 1e-9
             else:
                 assert abs(abs(r[k]) - np.sqrt(rad2) * abs(np.cos(2 * np.pi * u2))) < 1e-12
+
+
+def test_noise_streams_are_distinct(oracle_mod):
+    a = oracle_mod.normals(3, 10, 4, 0)
+    b = oracle_mod.normals(3, 10, 4, 1)
+    assert np.abs(a[4:] - b[4:]).min() > 0
+    box = oracle_mod.Box(4, 3, 2, 0.8, 1e-3, seed=3)
+    s1 = oracle_mod.Box(4, 3, 2, 0.8, 1e-3, seed=3, stream=1)
+    box.step(2)
+    s1.step(2)
+    assert np.abs(box.get_f() - s1.get_f()).max() > 1e-6
 
 
 def test_normals_are_standard_normal(oracle_mod):
