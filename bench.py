@@ -52,6 +52,17 @@ def parse_args(argv=None):
                     help="population storage (fp32 = the benchmark workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", choices=["box", "ensemble"], default="box",
+                    help="box: one 512^3 box (default); ensemble: 256 x 32^3 + 64 x 64^3 + "
+                         "8 x 128^3 replicas in one persistent kernel per step")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="ensemble: skip timing the same replicas one box at a time")
+    ap.add_argument("--ens-div", type=int, default=1,
+                    help="ensemble: divide every replica count by this (profiling runs; 1 = the "
+                         "benchmark workload)")
+    ap.add_argument("--tuning", type=int, nargs=4, default=None,
+                    metavar=("ITEM_NODES", "STAGES", "WARPS", "CTAS_PER_SM"),
+                    help="ensemble: this launch shape instead of the autotuner's")
     return ap.parse_args(argv)
 
 
@@ -421,12 +432,187 @@ def run_ours(args, rank, local, ws):
     return 0
 
 
+# ----------------------------------------------------------------------------
+# batched ensemble
+
+
+ENSEMBLE_SIZES = [32] * 256 + [64] * 64 + [128] * 8
+
+
+def ensemble_sizes(div=1):
+    return [32] * (256 // div) + [64] * (64 // div) + [128] * max(1, 8 // div)
+
+
+def ensemble_params(flbm, seed, sizes=None):
+    """The mixed ensemble: 256 x 32^3 + 64 x 64^3 + 8 x 128^3 periodic boxes,
+    tau uniform in [0.51, 3.0] (seeded), kT = 1e-5, rho0 = 1, GMF-FLBM, FP32,
+    one Philox key and one noise stream per replica."""
+    import numpy as np
+    sizes = ENSEMBLE_SIZES if sizes is None else sizes
+    rng = np.random.default_rng(seed)
+    taus = rng.uniform(0.51, 3.0, size=len(sizes))
+    return [flbm.make_params(n, n, n, float(t), WORKLOAD["kT"], rho0=WORKLOAD["rho0"], seed=seed,
+                             precision=flbm.FLBM_FP32, stats_every=1, noise_stream=r)
+            for r, (n, t) in enumerate(zip(sizes, taus))]
+
+
+def ensemble_config(ws, tuning=None, sizes=None):
+    sizes = ENSEMBLE_SIZES if sizes is None else sizes
+    nodes = sum(n ** 3 for n in sizes)
+    mix = " + ".join("%d x %d^3" % (sizes.count(n), n) for n in sorted(set(sizes)))
+    c = {"workload": "batched GMF-FLBM D3Q27 ensemble: %s periodic "
+                     "replicas (%d nodes), tau ~ U[0.51, 3.0], kT=1e-5, rho0=1, FP32 deviations AA "
+                     "in place, one noise stream per replica, FP64 per-replica reductions every "
+                     "step, one persistent kernel + one statistics kernel per step, CUDA graph"
+                     % (mix, nodes),
+         "replicas": len(sizes), "nodes": nodes, "scheme": "gmf", "kT": WORKLOAD["kT"],
+         "l2": "inputs larger than L2 (%.2f GB state vs 129 MB L2)" % (nodes * 108 / 1e9),
+         "parallelism": "replicas x%d (one independent ensemble per GPU)" % ws}
+    if tuning:
+        c["tuning"] = tuning
+    return c
+
+
+def run_ensemble(args, rank, local, ws):
+    import numpy as np
+    import torch
+    from paper_2601_03806_gb300 import build as _b
+    _b.build()
+    from paper_2601_03806_gb300 import flbm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seed = WORKLOAD["seed"] + rank
+    kT, rho0 = WORKLOAD["kT"], WORKLOAD["rho0"]
+    stream = torch.cuda.Stream(device=dev)
+    sizes = ensemble_sizes(args.ens_div)
+    params = ensemble_params(flbm, seed, sizes)
+    ens = flbm.Ensemble(params, stream=stream)
+    N = ens.nodes
+    if args.tuning:
+        ens.set_tuning(*args.tuning)
+        tuning = ens.tuning
+    else:
+        tuning = ens.autotune(steps_per_trial=3)
+    for r, rep in enumerate(ens.replicas):
+        rep.init_thermal(seed * 1000 + r)
+    ens.step(args.warmup + (args.warmup % 2))
+    for rep in ens.replicas:
+        rep.stats_reset()
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    gpu_id = ("GPU-" + str(uuid)) if uuid is not None else os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(ws)
+    with ClockSampler(gpu_id) as clk:
+        start.record(stream)
+        ens.step(args.steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    el_ms = start.elapsed_time(end)
+    max_ms = max_over_ranks(el_ms, ws, dev)
+    value = job_mlups(N, args.steps, max_ms, ws)
+    step_ms = el_ms / args.steps
+    peak, peak_src = measured_hbm_peak()
+    achieved = BYTES_PER_NODE["fp32"] * N / (step_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                "kernel": "flbm::k_step_ens<float,float,GMF,*,stats> + flbm::k_ens_post (per-step "
+                          "time of both, graph replay)",
+                "kernel_ms": step_ms, "algorithmic_bytes_per_launch": BYTES_PER_NODE["fp32"] * N}
+
+    # ensemble-averaged <u_a^2> per replica and S(k) flatness per box size
+    u2 = np.array([rep.stats()["u2_avg"] for rep in ens.replicas]) / (kT / rho0)
+    sk = {}
+    for n in sorted(set(sizes)):
+        r = sizes.index(n)
+        S, cnt = ens[r].structure_factor(flbm.FLBM_OBS_JX, n // 2)
+        m = cnt > 0
+        sk["%d^3" % n] = float(np.sum(S[m] * cnt[m]) / np.sum(cnt[m]) / (rho0 * kT))
+    equip = {"u2_avg_over_kT_rho0_mean": float(u2.mean()),
+             "max_abs_error_over_replicas": float(np.abs(u2 - 1).max()),
+             "samples_per_replica": args.steps,
+             "S_jx_mean_over_rho0_kT_first_replica_of_each_size": sk}
+
+    # the same replicas as independent boxes, one plain flbm_step call each
+    plain = None
+    if not args.no_plain:
+        boxes = [flbm.Lattice(p.nx, p.ny, p.nz, p.tau, p.kT, seed=p.seed, precision=flbm.FLBM_FP32,
+                              noise_stream=p.noise_stream, torch_memory=True, stream=stream)
+                 for p in params]
+        for b in boxes:
+            b.init_thermal(seed)
+            b.step(2)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for b in boxes:
+            b.step(args.steps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        p_ms = t0.elapsed_time(t1)
+        plain = {"value": N * args.steps / (p_ms / 1e3) / 1e6, "unit": "MLUPS",
+                 "what": "the same %d replicas as single-box contexts, flbm_step(K) on each in turn"
+                         % len(params)}
+        for b in boxes:
+            b.close()
+
+    e2e = None
+    if not args.no_e2e:
+        hstates = [torch.empty(27 * rep.n, dtype=torch.float32, pin_memory=True) for rep in ens.replicas]
+        for rep, h in zip(ens.replicas, hstates):
+            rep.get_state(h)
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for rep, h in zip(ens.replicas, hstates):
+            rep.set_state(h)
+        ens.step(args.steps)
+        stats = [rep.stats() for rep in ens.replicas]
+        torch.cuda.synchronize()
+        e_ms = (time.perf_counter() - t0) * 1e3
+        e_max = max_over_ranks(e_ms, ws, dev)
+        import ctypes
+        e2e = {"value": job_mlups(N, args.steps, e_max, ws), "unit": "MLUPS",
+               "h2d_bytes_per_step": 4 * 27 * N // args.steps,
+               "d2h_bytes_per_step": len(stats) * (ctypes.sizeof(flbm.flbm_stats_t) + 16),
+               "what": "flbm_set_state of every replica from pinned host + flbm_ensemble_step(K) + "
+                       "flbm_stats of every replica"}
+        del hstates
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, threads, steps, _ = oracle_sample(1.0, kT, rho0, WORKLOAD["seed"], n=32)
+        cpu = {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+               "sample": "one 32^3 replica (tau = 1.0, kT = 1e-5) from a thermal state, %d steps, "
+                         "FP64 two-array oracle on %d host threads" % (steps, threads)}
+    if rank == 0:
+        line = {
+            "metric": "MLUPS of the batched GMF-FLBM ensemble step (persistent kernel, CUDA graph)",
+            "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": ensemble_config(ws, tuning, sizes), "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": e2e, "plain_kernel": plain, "gpu_launches": 2 * int(args.steps),
+            "clocks": clk.summary(), "equipartition": equip,
+        }
+        print(json.dumps(line), flush=True)
+    ens.close()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     rank, local, ws = dist_setup()
     try:
         if args.impl == "reference":
             return run_reference(args, rank, ws)
+        if args.workload == "ensemble":
+            return run_ensemble(args, rank, local, ws)
         return run_ours(args, rank, local, ws)
     finally:
         if ws > 1:

@@ -32,7 +32,8 @@
  *     flbm_step returns after the launched steps completed (it reads the
  *     instability flag back).
  *   - Noise: Philox4x32-10 (Salmon et al., SC'11), key = (seed lo, seed hi),
- *     counter = (node, step lo, block j = 0..5, step hi); word m of block j
+ *     counter = (node, step lo, j | noise_stream << 8, step hi) for blocks
+ *     j = 0..5; word m of block j
  *     feeds mode k = 4 + 4j + m (mode 27 unused); Box-Muller on consecutive
  *     word pairs with u = ((w >> 9) + 0.5) 2^-23.  The result therefore does
  *     not depend on launch shape, and a checkpoint (populations + step +
@@ -93,7 +94,10 @@ typedef struct flbm_params {
     int32_t precision;     /* flbm_precision */
     int32_t noise_rho0;    /* 0: phi_k uses the local rho(x,t); 1: uses rho0 */
     int32_t stats_every;   /* fused FP64 reductions every k-th step (0: off) */
-    int32_t reserved;      /* must be 0 */
+    int32_t noise_stream;  /* noise stream id s, 0 <= s < 2^24: the Philox
+                              counter word 2 is block | s << 8, so boxes under
+                              one seed with distinct streams draw independent
+                              noise (0: the default stream) */
     double tau;            /* relaxation time, > 0.5 (omega = 1/tau) */
     double kT;             /* thermal energy k_B T >= 0 (lattice units) */
     double rho0;           /* reference density > 0; initial state f_i = w_i rho0 */
@@ -246,8 +250,95 @@ const char *flbm_last_error(const flbm_ctx *c);
 int flbm_step_noalloc(const flbm_params *p, void *dev_state, int64_t step, int parity,
                       double *dev_sums, void *cuda_stream);
 
-/* Release everything the context owns (not a caller dev_buf/stream). */
+/* Release everything the context owns (not a caller dev_buf/stream).  A
+ * replica context of an ensemble is left alone (the ensemble owns it). */
 void flbm_destroy(flbm_ctx *c);
+
+/* ------------------------------------------------------------------------
+ * Batched ensemble: many independent periodic boxes (replicas) of uneven
+ * sizes, taus and noise streams advanced together by one persistent kernel
+ * per step, for the ensemble averages that equilibrium fluctuation
+ * statistics need (Sec. III measures <u^2> and S(k) as averages).  The
+ * paper runs one box at a time; the ensemble is this library's.  Every
+ * replica evolves as the single box of the same flbm_params would (the same
+ * noise; equal to the rounding of the storage type, as the two kernels fuse
+ * multiply-adds differently), and the results do not depend on the launch
+ * shape or on whether steps replay from the CUDA graph (bit for bit).
+ *
+ * Work decomposition: replica r is cut into items of whole x-rows of one
+ * z-plane (about item_nodes nodes); all items of all replicas are split into
+ * equal contiguous chunks, one per CTA of a persistent grid.  The replica
+ * populations live in one device buffer, replica after replica, each in the
+ * single-box layout (SoA deviation planes, AA pattern in place).  A step
+ * is two launches (the step kernel and a small per-replica statistics
+ * kernel that also advances a device step counter), and runs of steps are
+ * replayed from a captured CUDA graph. */
+typedef struct flbm_ensemble flbm_ensemble;   /* opaque, owned by the library */
+
+/* Launch shape of the ensemble step kernel. */
+typedef struct flbm_ensemble_tuning {
+    int32_t item_nodes;     /* target nodes per work item, 32..4096: rows per
+                               item = the largest divisor of ny with
+                               rows * nx <= max(item_nodes, nx) */
+    int32_t stages;         /* items in flight per CTA (shared-memory stages), 2..4 */
+    int32_t compute_warps;  /* collision warps per CTA, 1..8 (plus one copy warp) */
+    int32_t ctas_per_sm;    /* resident CTAs per SM, >= 1 (capped by occupancy) */
+    double ms_per_step;     /* flbm_ensemble_autotune: measured time of the shape;
+                               otherwise 0 */
+} flbm_ensemble_tuning;
+
+/* Create an ensemble of `count` replicas, params[r] describing replica r.
+ * All replicas share scheme, precision (FLBM_FP32 or FLBM_FP16; FLBM_FP64
+ * gives FLBM_E_UNSUPPORTED), stats_every and seed (one Philox key) and have
+ * pairwise distinct noise_stream values, so their noise is independent;
+ * tau, kT, rho0, noise_rho0 and the box may differ.  Each nx must be a
+ * multiple of 32 (16-byte bulk copies) with 54 nx element bytes <= 200 KiB,
+ * and N < 2^31.  State f_i = w_i rho0 at step 0.  cuda_stream: NULL for a
+ * library-owned stream, else a cudaStream_t of the current device (not the
+ * legacy default stream).  Default launch shape: item_nodes 256, stages 2,
+ * compute_warps 8, ctas_per_sm 2. */
+int flbm_ensemble_create(const flbm_params *params, int count, void *cuda_stream,
+                         flbm_ensemble **out);
+
+/* Borrowed context of replica `index` (valid until flbm_ensemble_destroy):
+ * every read call of flbm_ctx works on it (moments, stats, structure factor,
+ * populations, probe, state, params, step).  flbm_step and flbm_set_step on
+ * it give FLBM_E_INVALID; its state may be replaced (set_populations,
+ * set_state, init_thermal) only at an even ensemble step. */
+int flbm_ensemble_replica(flbm_ensemble *e, int index, flbm_ctx **out);
+
+/* Advance every replica by n >= 0 steps; returns after they completed.
+ * Runs of whole graph periods (2 steps, or lcm(2, stats_every) <= 64) are
+ * replayed from a CUDA graph when graphs are enabled.  FLBM_E_UNSTABLE names
+ * the first failing replica; FLBM_E_TIMEOUT as for flbm_step. */
+int flbm_ensemble_step(flbm_ensemble *e, int64_t n);
+
+/* Use (1, default) or bypass (0) the CUDA graph in flbm_ensemble_step. */
+int flbm_ensemble_graph(flbm_ensemble *e, int enable);
+
+/* Set / read the launch shape.  FLBM_E_INVALID if it does not fit the
+ * device (shared memory, occupancy) or is out of range. */
+int flbm_ensemble_set_tuning(flbm_ensemble *e, const flbm_ensemble_tuning *t);
+int flbm_ensemble_get_tuning(const flbm_ensemble *e, flbm_ensemble_tuning *out);
+
+/* Time every valid shape of item_nodes {128, 256, 512} x stages {2, 3, 4} x
+ * compute_warps {4, 8} x ctas_per_sm {1, 2} over steps_per_trial >= 1 steps
+ * (after 2 warm-up steps) and keep the fastest (written to *best if not
+ * NULL).  Only at step 0 (FLBM_E_INVALID otherwise); the trials advance the
+ * replicas, so afterwards every replica is reset to f_i = w_i rho0, the
+ * statistics are cleared and the step counter is 0 again.  Results never
+ * depend on the launch shape. */
+int flbm_ensemble_autotune(flbm_ensemble *e, int steps_per_trial, flbm_ensemble_tuning *best);
+
+int flbm_ensemble_count(const flbm_ensemble *e);        /* replicas; -1 on NULL */
+int64_t flbm_ensemble_get_step(const flbm_ensemble *e); /* -1 on NULL */
+
+/* Error text of the last failing call on e; e == NULL gives the thread's
+ * last create-time error. */
+const char *flbm_ensemble_last_error(const flbm_ensemble *e);
+
+/* Release the ensemble and its replica contexts (not a caller stream). */
+void flbm_ensemble_destroy(flbm_ensemble *e);
 
 #ifdef __cplusplus
 }

@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "internal.h"
+#include "stats.cuh"
 #include "lattice.cuh"
 
 namespace flbm {
@@ -339,15 +340,9 @@ __global__ void k_stats_finalize(const double *partials, int nblocks, DevStats *
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NSTAT; ++s) st->last[s] = red[s][0];
-        for (int a = 0; a < 3; ++a) st->acc_u2[a] += red[S_UX2 + a][0] / n;
-        st->acc_m[0] += red[S_DRHO][0] / n;
-        st->acc_m[1] += (red[S_JX][0] + red[S_JY][0] + red[S_JZ][0]) / n;
-        st->acc_m[2] += red[S_M3][0] / n;
-        st->acc_m[3] += red[S_M4][0] / n;
-        for (int k = 0; k < 4; ++k) st->acc_m2[k] += red[S_M1SQ + k][0] / n;
-        st->step = step;
-        st->nsamp += 1;
+        double tot[NSTAT];
+        for (int s = 0; s < NSTAT; ++s) tot[s] = red[s][0];
+        stats_update(st, tot, step, n);
     }
 }
 

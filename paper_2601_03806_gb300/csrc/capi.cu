@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/flbm.h"
+#include "ctx.h"
 #include "internal.h"
 #include "lattice.cuh"
 
@@ -25,55 +26,9 @@ namespace {
 
 thread_local std::string g_create_error;
 
-struct DevFlags {
-    unsigned int flag;
-    unsigned int pad;
-    unsigned long long bad_step;
-};
-
 constexpr uint64_t kChunkNodes = 1ull << 20;   // nodes per host-transfer chunk
 
 }  // namespace
-
-struct flbm_ctx {
-    flbm_params p{};
-    int device = 0;
-    int nsm = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    void *g = nullptr;
-    bool own_g = false;
-    size_t g_bytes = 0;
-    uint64_t n = 0;
-    int64_t step = 0;
-    int phase = 0;                 // storage is natural when ((step + phase) & 1) == 0
-    uint32_t tx_pad = 0;           // failure injection into the row pipeline (tests)
-    int grid = 1;                  // persistent grid of the direct step kernel
-    int row_grid = 0;              // persistent grid of the TMA row pipeline (0: unused)
-    double *partials = nullptr;    // [max(grid, row_grid)][NSTAT]
-    DevStats *dstats = nullptr;
-    DevFlags *dflags = nullptr;
-    // host transfers: two staging buffers of pipe_nodes * 27 doubles, a copy
-    // stream, and events that hand each buffer between the streams
-    double *pipe[2] = {nullptr, nullptr};
-    uint64_t pipe_nodes = 0;
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_ready[2] = {nullptr, nullptr};
-    cudaEvent_t ev_free[2] = {nullptr, nullptr};
-    // S(k)
-    cufftHandle plan = 0;
-    bool has_plan = false;
-    void *fft_in = nullptr;
-    void *fft_out = nullptr;
-    double *shell_s = nullptr;
-    unsigned long long *shell_c = nullptr;
-    int shell_cap = 0;
-    // step-kernel timing
-    bool timing = false;
-    std::vector<cudaEvent_t> ev;   // pairs (start, stop), reused
-    size_t ev_used = 0;            // pairs recorded since the last read
-    std::string err;
-};
 
 namespace {
 
@@ -116,7 +71,9 @@ BoxDesc box_of(const flbm_ctx *c)
     return b;
 }
 
-std::string validate(const flbm_params *p)
+}  // namespace
+
+std::string flbm::validate_params(const flbm_params *p)
 {
     if (!p) return "params is NULL";
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "nx, ny, nz must be >= 1";
@@ -129,9 +86,11 @@ std::string validate(const flbm_params *p)
     if (p->precision < FLBM_FP64 || p->precision > FLBM_FP16) return "unknown precision";
     if (p->stats_every < 0) return "stats_every must be >= 0";
     if (p->noise_rho0 != 0 && p->noise_rho0 != 1) return "noise_rho0 must be 0 or 1";
-    if (p->reserved != 0) return "reserved must be 0";
+    if (p->noise_stream < 0 || p->noise_stream >= (1 << 24)) return "noise_stream must be in [0, 2^24)";
     return "";
 }
+
+namespace {
 
 // Relaxation and noise scalars of Eq. flbe2 (GMF), Eq. flbe (BGK) and
 // Reg-FLBM: post-collision M_k = a_eq,k + lambda_k (m_k - a_eq,k) + phi_k r_k
@@ -161,6 +120,12 @@ void fill_constants_t(const flbm_params &p, StepArgs<R> &a)
         a.rk[2 * r + 1] = k1;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
+    }
+    a.ctr2 = uint32_t(p.noise_stream) << 8;
+    for (int b = 0; b < 6; ++b) {
+        const uint64_t m = uint64_t(0xCD9E8D57u) * (uint32_t(b) | a.ctr2);
+        a.c2hk[b] = uint32_t(m >> 32) ^ a.rk[0];
+        a.c2lo[b] = uint32_t(m);
     }
     a.noise_rho0 = p.noise_rho0;
     a.rho0 = R(p.rho0);
@@ -256,7 +221,9 @@ int h2d_chunks(flbm_ctx *c, Copy copy, Consume consume)
     return FLBM_OK;
 }
 
-void release(flbm_ctx *c)
+}  // namespace
+
+void flbm::destroy_ctx(flbm_ctx *c)
 {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
@@ -281,11 +248,11 @@ void release(flbm_ctx *c)
     delete c;
 }
 
-int create_impl(const flbm_params *p, void *dev_buf, size_t dev_bytes, void *stream, flbm_ctx **out)
+int flbm::create_ctx(const flbm_params *p, void *dev_buf, size_t dev_bytes, void *stream, flbm_ctx **out)
 {
     if (!out) return fail(nullptr, FLBM_E_INVALID, "out is NULL");
     *out = nullptr;
-    const std::string why = validate(p);
+    const std::string why = validate_params(p);
     if (!why.empty()) return fail(nullptr, FLBM_E_INVALID, why);
     flbm_ctx *c = new (std::nothrow) flbm_ctx;
     if (!c) return fail(nullptr, FLBM_E_NOMEM, "host allocation failed");
@@ -295,7 +262,7 @@ int create_impl(const flbm_params *p, void *dev_buf, size_t dev_bytes, void *str
     int rc = FLBM_OK;
     auto bail = [&](int code) {
         g_create_error = c->err;
-        release(c);
+        destroy_ctx(c);
         return code;
     };
     cudaError_t e = cudaGetDevice(&c->device);
@@ -374,8 +341,6 @@ int create_impl(const flbm_params *p, void *dev_buf, size_t dev_bytes, void *str
     return FLBM_OK;
 }
 
-}  // namespace
-
 namespace flbm {
 void fill_step_constants(const flbm_params &p, StepArgs<float> &a) { fill_constants_t<float>(p, a); }
 void fill_step_constants(const flbm_params &p, StepArgs<double> &a) { fill_constants_t<double>(p, a); }
@@ -405,7 +370,7 @@ int flbm_params_init(flbm_params *p, int nx, int ny, int nz, double tau, double 
 
 size_t flbm_state_bytes(const flbm_params *p)
 {
-    if (!validate(p).empty()) return 0;
+    if (!validate_params(p).empty()) return 0;
     return uint64_t(p->nx) * uint64_t(p->ny) * uint64_t(p->nz) * kQ * elem_size(p->precision);
 }
 
@@ -414,18 +379,19 @@ int flbm_create(int nx, int ny, int nz, double tau, double kT, double rho0, uint
 {
     flbm_params p;
     flbm_params_init(&p, nx, ny, nz, tau, kT, rho0, seed, scheme);
-    return create_impl(&p, nullptr, 0, nullptr, out);
+    return create_ctx(&p, nullptr, 0, nullptr, out);
 }
 
 int flbm_create_ex(const flbm_params *p, void *dev_buf, size_t dev_bytes, void *cuda_stream,
                    flbm_ctx **out)
 {
-    return create_impl(p, dev_buf, dev_bytes, cuda_stream, out);
+    return create_ctx(p, dev_buf, dev_bytes, cuda_stream, out);
 }
 
 int flbm_step(flbm_ctx *c, int64_t n)
 {
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (c->ens) return fail(c, FLBM_E_INVALID, "an ensemble replica is stepped by flbm_ensemble_step");
     if (n < 0) return fail(c, FLBM_E_INVALID, "n must be >= 0");
     const int every = c->p.stats_every;
     for (int64_t s = 0; s < n; ++s) {
@@ -600,10 +566,36 @@ int flbm_get_populations(flbm_ctx *c, double *f)
         });
 }
 
+}  // extern "C"
+
+namespace {
+
+// An ensemble replica's state may be replaced only while the ensemble's
+// storage is in the natural form (every replica shares the AA parity).
+int replica_state_check(flbm_ctx *c)
+{
+    if (c->ens && parity(c) != 0)
+        return fail(c, FLBM_E_INVALID,
+                    "an ensemble replica's state can be replaced only when its storage is in the "
+                    "natural form (an even number of ensemble steps since the last replacement)");
+    return FLBM_OK;
+}
+
+int state_replaced(flbm_ctx *c)
+{
+    if (c->ens) ensemble_state_replaced(c->ens);
+    return FLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int flbm_set_populations(flbm_ctx *c, const double *f)
 {
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
     if (!f) return fail(c, FLBM_E_INVALID, "f is NULL");
+    if (int rc = replica_state_check(c)) return rc;
     BoxDesc b = box_of(c);
     b.parity = 0;
     const uint64_t N = c->n;
@@ -622,12 +614,13 @@ int flbm_set_populations(flbm_ctx *c, const double *f)
     rc = reset_flags(c);
     if (rc) return rc;
     CK(c, cudaStreamSynchronize(c->stream));
-    return FLBM_OK;
+    return state_replaced(c);
 }
 
 int flbm_init_thermal(flbm_ctx *c, uint64_t seed)
 {
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (int rc = replica_state_check(c)) return rc;
     BoxDesc b = box_of(c);
     b.parity = 0;
     CK(c, launch_init_thermal(c->g, prec_code(c), b, c->p.kT, seed, c->stream));
@@ -635,7 +628,7 @@ int flbm_init_thermal(flbm_ctx *c, uint64_t seed)
     int rc = reset_flags(c);
     if (rc) return rc;
     CK(c, cudaStreamSynchronize(c->stream));
-    return FLBM_OK;
+    return state_replaced(c);
 }
 
 int flbm_probe(flbm_ctx *c, const int64_t *nodes, int64_t count, double *f)
@@ -690,12 +683,13 @@ int flbm_set_state(flbm_ctx *c, const void *host)
 {
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
     if (!host) return fail(c, FLBM_E_INVALID, "host is NULL");
+    if (int rc = replica_state_check(c)) return rc;
     CK(c, cudaMemcpyAsync(c->g, host, c->g_bytes, cudaMemcpyHostToDevice, c->stream));
     c->phase = int(c->step & 1);
     int rc = reset_flags(c);
     if (rc) return rc;
     CK(c, cudaStreamSynchronize(c->stream));
-    return FLBM_OK;
+    return state_replaced(c);
 }
 
 int flbm_timing_enable(flbm_ctx *c, int enable)
@@ -729,6 +723,7 @@ int flbm_set_step(flbm_ctx *c, int64_t step)
 {
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
     if (step < 0) return fail(c, FLBM_E_INVALID, "step must be >= 0");
+    if (c->ens) return fail(c, FLBM_E_INVALID, "an ensemble replica follows the ensemble's step");
     const int par = parity(c);
     c->step = step;
     c->phase = int((par - (step & 1)) & 1);
@@ -747,6 +742,10 @@ const char *flbm_last_error(const flbm_ctx *c)
     return c ? c->err.c_str() : g_create_error.c_str();
 }
 
-void flbm_destroy(flbm_ctx *c) { release(c); }
+void flbm_destroy(flbm_ctx *c)
+{
+    if (c && c->ens) return;   // a replica lives and dies with its ensemble
+    destroy_ctx(c);
+}
 
 }  // extern "C"

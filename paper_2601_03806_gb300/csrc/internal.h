@@ -34,6 +34,9 @@ struct StepArgs {
     uint64_t nchunks;             // cpr * ny * nz
     uint64_t step;                // t of this collision (noise counter)
     uint32_t rk[20];              // Philox round keys (k0, k1) of rounds 0..9
+    uint32_t ctr2;                // noise stream id << 8 (Philox counter word 2 = block | ctr2)
+    uint32_t c2hk[6], c2lo[6];    // Philox round 0 of word 2 = block | ctr2 for blocks 0..5:
+                                  // hi(M1 (block | ctr2)) ^ rk[0] and lo(M1 (block | ctr2))
     int32_t noise_rho0;           // phi_k uses rho0 instead of rho(x,t)
     uint32_t tx_pad;              // failure injection: bytes the row pipeline
                                   // expects beyond what it copies (0 normally)
@@ -59,6 +62,69 @@ struct DevStats {
     long long step;        // t of the most recent reduced step
     long long nsamp;       // reduced steps since reset
 };
+
+// ---------------------------------------------------------------------------
+// Batched ensemble (ens_kernel.cuh): many independent periodic boxes advanced
+// by one persistent kernel.  Each replica is cut into work items of rpi whole
+// x-rows of one z-plane (rpi divides ny); the items of all replicas form one
+// global sequence that the CTAs split into contiguous, equal-length chunks.
+
+// One replica, as the kernels see it (device table, host-built).
+struct EnsReplica {
+    void *g;                      // its deviation planes g[i*n + node]
+    uint64_t n;                   // nodes
+    uint64_t item0;               // global index of its first item
+    uint32_t nx, ny, nz;
+    uint32_t rpi;                 // x-rows per item (divides ny)
+    uint32_t item_nodes;          // rpi * nx
+    uint32_t items_per_plane;     // ny / rpi
+    uint32_t ctr2;                // noise stream << 8
+    int32_t noise_rho0;
+    double rho0, sqrt_rho0;       // the scalars of StepArgs, per replica
+    double lambda, omega, amp_h, amp_g;
+    int32_t cta_lo, cta_hi;       // CTAs whose chunks meet this replica
+    DevStats *st;                 // accumulators of the replica's context
+    unsigned long long *bad_step; // first unstable step of this replica
+};
+
+struct EnsArgs {
+    uint32_t rk[20];              // Philox round keys (one key for the ensemble)
+    const EnsReplica *reps;
+    uint32_t nrep;
+    uint32_t stages;              // shared-memory stages per CTA (2..kEnsMaxStages)
+    uint32_t stride;              // elements per staged segment (>= every item_nodes)
+    uint32_t tx_pad;              // failure injection (0 normally)
+    uint64_t nitems;              // items of all replicas
+    const unsigned long long *dstep;   // t of this step (advanced by the post kernel)
+    double *partials;             // [grid + nrep][NSTAT]: slot (cta + replica)
+    unsigned int *flag;           // bit 0: instability; bit 1: a bounded wait ran out
+};
+constexpr int kEnsMaxStages = 4;
+constexpr int kEnsMaxWarps = 8;    // compute warps per CTA at most
+
+// Chunk [begin, end) of the global item sequence owned by CTA b of grid.
+__host__ __device__ inline void ens_chunk(uint64_t nitems, uint32_t b, uint32_t grid, uint64_t &begin,
+                                          uint64_t &end)
+{
+    const uint64_t k = nitems / grid, rem = nitems % grid;
+    begin = uint64_t(b) * k + (uint64_t(b) < rem ? uint64_t(b) : rem);
+    end = begin + k + (uint64_t(b) < rem ? 1u : 0u);
+}
+
+// Launchers (ens_f32.cu, ens_f16.cu): the step kernel with `threads` threads
+// (compute warps + one copy warp) and `smem` dynamic shared bytes, and its
+// resident CTAs per SM (0 if the shape does not fit; also sets the kernels'
+// shared-memory attribute on the current device).
+cudaError_t launch_ens_step_f32(const EnsArgs &a, int scheme, bool odd, bool stats, int grid,
+                                int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_ens_step_f16(const EnsArgs &a, int scheme, bool odd, bool stats, int grid,
+                                int threads, size_t smem, cudaStream_t s);
+int ens_occupancy_f32(int scheme, int threads, size_t smem);
+int ens_occupancy_f16(int scheme, int threads, size_t smem);
+// After each ensemble step: per-replica FP64 totals of the partial slots into
+// each replica's DevStats (stats steps), then the step counter advances.
+cudaError_t launch_ens_post(const EnsArgs &a, bool stats, uint32_t cwarps, unsigned int *done,
+                            unsigned long long *dstep, cudaStream_t s);
 
 // Step-kernel launchers (step_f64.cu, step_f32.cu).  grid: CTAs of the
 // direct kernel; row_grid: CTAs of the TMA row pipeline (0: do not use it).

@@ -155,6 +155,25 @@ __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, const uint32_t (&rk)[20]
     return c;
 }
 
+// The same block function with round 0's product of counter word 2 supplied
+// by the caller: h2k = hi(0xCD9E8D57 * c.z) ^ rk[0], l2 = lo(0xCD9E8D57 * c.z).
+// When c.z is uniform over a launch (block index | stream << 8) the host
+// computes the pair once, and the kernel reads it as a constant.
+__device__ __forceinline__ u32x4 philox4x32_10_r0(uint32_t c0, uint32_t c1, uint32_t c3, uint32_t h2k,
+                                                  uint32_t l2, const uint32_t (&rk)[20])
+{
+    const uint64_t p0 = uint64_t(0xD2511F53u) * c0;
+    u32x4 c{h2k ^ c1, l2, uint32_t(p0 >> 32) ^ c3 ^ rk[1], uint32_t(p0)};
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        const uint64_t q0 = uint64_t(0xD2511F53u) * c.x;
+        const uint64_t q1 = uint64_t(0xCD9E8D57u) * c.z;
+        c = u32x4{uint32_t(q1 >> 32) ^ c.y ^ rk[2 * r], uint32_t(q1),
+                  uint32_t(q0 >> 32) ^ c.w ^ rk[2 * r + 1], uint32_t(q0)};
+    }
+    return c;
+}
+
 // 23-bit uniform in (0,1): ((w >> 9) + 0.5) 2^-23, exact in float and double.
 // FP32 builds it from the bits: (1 + m 2^-23) - (1 - 2^-24) is exact.
 __device__ __forceinline__ float uniform23f(uint32_t w)

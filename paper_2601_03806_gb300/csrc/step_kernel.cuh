@@ -17,7 +17,8 @@
 //   a5  ghost modes k = 10..26: no deterministic content (GMF); (1-omega) m_k
 //       for BGK-FLBM (Eq. flbe); rho u^(deg) for Reg-FLBM
 //   a6  M_k += phi_k r_k  (Eqs. fluct_phi / fluct_phig), r_k from
-//       Philox4x32-10 keyed on (seed; node, step, block) + Box-Muller
+//       Philox4x32-10 keyed on (seed; node, step, block | stream << 8) +
+//       Box-Muller
 //   a7  f*_i = w_i sum_k e_ki M_k / b_k (three 1-D passes), minus w_i rho0
 //   a9  optional per-thread partial sums for the FP64 reductions
 //
@@ -155,13 +156,31 @@ __device__ __forceinline__ void block_reduce_store(const R (&acc)[NSTAT], double
 
 constexpr int kNoise = kQ - 4;
 
+// Philox block blk of node at the step: counter (node, step lo, blk | stream
+// << 8, step hi).  ctr2_round0 supplies round 0's product of counter word 2:
+// host-precomputed kernel constants for one box; per replica in an ensemble.
 template <typename R>
-__device__ __forceinline__ void draw_noise(const StepArgs<R> &a, uint32_t node, R (&nz)[kNoise])
+__device__ __forceinline__ void ctr2_round0(const StepArgs<R> &a, int blk, uint32_t &h2k, uint32_t &l2)
+{
+    h2k = a.c2hk[blk];
+    l2 = a.c2lo[blk];
+}
+template <typename A>
+__device__ __forceinline__ u32x4 noise_block(const A &a, uint32_t node, int blk)
+{
+    uint32_t h2k, l2;
+    ctr2_round0(a, blk, h2k, l2);
+    return philox4x32_10_r0(node, uint32_t(a.step), uint32_t(a.step >> 32), h2k, l2, a.rk);
+}
+
+// A is the step's scalar set: StepArgs<R> for one box, or a per-replica view
+// with the same member names (rk, step, ctr2, rho0, ...) for an ensemble.
+template <typename R, typename A>
+__device__ __forceinline__ void draw_noise(const A &a, uint32_t node, R (&nz)[kNoise])
 {
 #pragma unroll
     for (int blk = 0; blk < 6; ++blk) {
-        const u32x4 o = philox4x32_10(
-            u32x4{node, uint32_t(a.step), uint32_t(blk), uint32_t(a.step >> 32)}, a.rk);
+        const u32x4 o = noise_block(a, node, blk);
         R rad0, c0, s0, rad1, c1, s1;
         box_muller(o.x, o.y, rad0, c0, s0);
         box_muller(o.z, o.w, rad1, c1, s1);
@@ -186,8 +205,8 @@ __device__ __forceinline__ void draw_noise(const StepArgs<R> &a, uint32_t node, 
 // populations arrived); otherwise the normals of `node` are drawn here pair
 // by pair and folded in at once (fewer live registers).
 
-template <typename R, int SCHEME, bool STATS, bool PREDRAWN>
-__device__ __forceinline__ void collide_core(R (&v)[3][3][3], const StepArgs<R> &a,
+template <typename R, int SCHEME, bool STATS, bool PREDRAWN, typename A>
+__device__ __forceinline__ void collide_core(R (&v)[3][3][3], const A &a,
                                              const R (&nz)[kNoise], uint32_t node, R (&acc)[NSTAT])
 {
     // a2: forward Hermite projection, three 1-D passes
@@ -290,8 +309,7 @@ __device__ __forceinline__ void collide_core(R (&v)[3][3][3], const StepArgs<R> 
             // pairs never mix hydrodynamic and ghost modes
 #pragma unroll
             for (int blk = 0; blk < 6; ++blk) {
-                const u32x4 o = philox4x32_10(
-                    u32x4{node, uint32_t(a.step), uint32_t(blk), uint32_t(a.step >> 32)}, a.rk);
+                const u32x4 o = noise_block(a, node, blk);
                 R rad0, c0, s0, rad1, c1, s1;
                 box_muller(o.x, o.y, rad0, c0, s0);
                 box_muller(o.z, o.w, rad1, c1, s1);
@@ -634,6 +652,9 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) <= 4 ? 2 : 1)
 // ---------------------------------------------------------------------------
 // launchers
 
+// Dynamic shared memory of a row-pipeline CTA at most.
+constexpr size_t kRowMaxSmem = 200 * 1024;
+
 // Whether the row pipeline serves a box of row length nx, and its CTA shape.
 struct RowPlan {
     bool use = false;
@@ -645,7 +666,7 @@ inline RowPlan row_plan(uint32_t nx)
 {
     RowPlan p;
     const size_t smem = kRowStages * row_stage_bytes<S>(nx);
-    if (nx % 32 != 0 || nx < 32 || smem > 200 * 1024) return p;
+    if (nx % 32 != 0 || nx < 32 || smem > kRowMaxSmem) return p;
     const uint32_t npt = (nx + kRowCompute - 1) / kRowCompute;
     uint32_t thr = (nx + npt - 1) / npt;
     thr = (thr + 31) / 32 * 32;
@@ -706,7 +727,9 @@ void prepare_scheme(uint32_t nx, bool stats, int &direct, int &rows)
     if (e == cudaSuccess && nb > 0) direct = nb;
     const RowPlan rp = row_plan<S>(nx);
     if (!rp.use) return;
-    const int sm = int(rp.smem);
+    // the attribute is per kernel, shared by every context of the process:
+    // set it to the largest staging any box may use, not to this box's
+    const int sm = int(kRowMaxSmem);
     cudaFuncSetAttribute(k_step_rows<S, R, SC, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_step_rows<S, R, SC, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_step_rows<S, R, SC, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);

@@ -32,7 +32,7 @@ class flbm_params(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("scheme", C.c_int32), ("precision", C.c_int32),
                 ("noise_rho0", C.c_int32), ("stats_every", C.c_int32),
-                ("reserved", C.c_int32), ("tau", C.c_double), ("kT", C.c_double),
+                ("noise_stream", C.c_int32), ("tau", C.c_double), ("kT", C.c_double),
                 ("rho0", C.c_double), ("seed", C.c_uint64)]
 
 
@@ -45,6 +45,14 @@ class flbm_stats_t(C.Structure):
         return {"step": self.step, "n_samples": self.n_samples, "mass": self.mass,
                 "mom": list(self.mom), "u2": list(self.u2), "u2_avg": list(self.u2_avg),
                 "m_mean": list(self.m_mean), "m_var": list(self.m_var), "er": list(self.er)}
+
+
+class flbm_ensemble_tuning(C.Structure):
+    _fields_ = [("item_nodes", C.c_int32), ("stages", C.c_int32), ("compute_warps", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("ms_per_step", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class FlbmError(RuntimeError):
@@ -84,6 +92,17 @@ def _load():
         "flbm_last_error": ([vp], C.c_char_p),
         "flbm_destroy": ([vp], None),
         "flbm_step_noalloc": ([P(flbm_params), vp, i64, i32, vp, vp], i32),
+        "flbm_ensemble_create": ([P(flbm_params), i32, vp, P(vp)], i32),
+        "flbm_ensemble_replica": ([vp, i32, P(vp)], i32),
+        "flbm_ensemble_step": ([vp, i64], i32),
+        "flbm_ensemble_graph": ([vp, i32], i32),
+        "flbm_ensemble_set_tuning": ([vp, P(flbm_ensemble_tuning)], i32),
+        "flbm_ensemble_get_tuning": ([vp, P(flbm_ensemble_tuning)], i32),
+        "flbm_ensemble_autotune": ([vp, i32, P(flbm_ensemble_tuning)], i32),
+        "flbm_ensemble_count": ([vp], i32),
+        "flbm_ensemble_get_step": ([vp], i64),
+        "flbm_ensemble_last_error": ([vp], C.c_char_p),
+        "flbm_ensemble_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -118,6 +137,17 @@ flbm_get_params = lib.flbm_get_params
 flbm_last_error = lib.flbm_last_error
 flbm_destroy = lib.flbm_destroy
 flbm_step_noalloc = lib.flbm_step_noalloc
+flbm_ensemble_create = lib.flbm_ensemble_create
+flbm_ensemble_replica = lib.flbm_ensemble_replica
+flbm_ensemble_step = lib.flbm_ensemble_step
+flbm_ensemble_graph = lib.flbm_ensemble_graph
+flbm_ensemble_set_tuning = lib.flbm_ensemble_set_tuning
+flbm_ensemble_get_tuning = lib.flbm_ensemble_get_tuning
+flbm_ensemble_autotune = lib.flbm_ensemble_autotune
+flbm_ensemble_count = lib.flbm_ensemble_count
+flbm_ensemble_get_step = lib.flbm_ensemble_get_step
+flbm_ensemble_last_error = lib.flbm_ensemble_last_error
+flbm_ensemble_destroy = lib.flbm_ensemble_destroy
 
 
 def _ptr(a: np.ndarray):
@@ -125,69 +155,23 @@ def _ptr(a: np.ndarray):
 
 
 def make_params(nx, ny, nz, tau, kT, rho0=1.0, seed=0, scheme=FLBM_GMF, precision=FLBM_FP32,
-                noise_rho0=False, stats_every=1) -> flbm_params:
+                noise_rho0=False, stats_every=1, noise_stream=0) -> flbm_params:
     p = flbm_params()
     lib.flbm_params_init(C.byref(p), nx, ny, nz, tau, kT, rho0, seed,
                          SCHEMES.get(scheme, scheme) if isinstance(scheme, str) else scheme)
     p.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
     p.noise_rho0 = int(bool(noise_rho0))
     p.stats_every = int(stats_every)
+    p.noise_stream = int(noise_stream)
     return p
 
 
-class Lattice:
-    """Owning wrapper of one flbm_ctx.
-
-    torch_memory=True: the population buffer is a torch CUDA tensor and the
-    work is ordered on torch's current stream (``self.stream``)."""
-
-    def __init__(self, nx, ny, nz, tau, kT, rho0=1.0, seed=0, scheme=FLBM_GMF,
-                 precision=FLBM_FP32, noise_rho0=False, stats_every=1, torch_memory=False,
-                 stream=None):
-        self.params = make_params(nx, ny, nz, tau, kT, rho0, seed, scheme, precision,
-                                  noise_rho0, stats_every)
-        self.nx, self.ny, self.nz = nx, ny, nz
-        self.n = nx * ny * nz
-        self._h = C.c_void_p()
-        self._buf = None
-        self.stream = stream
-        dev, nbytes, sp = None, 0, None
-        if torch_memory:
-            import torch
-            nbytes = int(lib.flbm_state_bytes(C.byref(self.params)))
-            if nbytes == 0:
-                raise FlbmError(FLBM_E_INVALID, "invalid parameters")
-            self._buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-            dev = self._buf.data_ptr()
-            if self.stream is None:
-                self.stream = torch.cuda.current_stream()
-        if self.stream is not None:
-            sp = self.stream.cuda_stream if hasattr(self.stream, "cuda_stream") else int(self.stream)
-        rc = lib.flbm_create_ex(C.byref(self.params), dev, nbytes, sp, C.byref(self._h))
-        if rc != FLBM_OK:
-            raise FlbmError(rc, lib.flbm_last_error(None).decode())
+class _CtxOps:
+    """Calls on one flbm_ctx (self._h, self.params, self.nx/ny/nz)."""
 
     def _check(self, rc):
         if rc != FLBM_OK:
             raise FlbmError(rc, lib.flbm_last_error(self._h).decode())
-
-    def close(self):
-        if self._h:
-            lib.flbm_destroy(self._h)
-            self._h = C.c_void_p()
-        self._buf = None
-
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
-
-    def __enter__(self):
-        return self
-
-    def __exit__(self, *exc):
-        self.close()
 
     @property
     def handle(self):
@@ -272,3 +256,142 @@ class Lattice:
             self._check(lib.flbm_set_state(self._h, _ptr(gg)))
         else:  # a pinned torch tensor
             self._check(lib.flbm_set_state(self._h, C.c_void_p(g.data_ptr())))
+
+
+class Lattice(_CtxOps):
+    """Owning wrapper of one flbm_ctx.
+
+    torch_memory=True: the population buffer is a torch CUDA tensor and the
+    work is ordered on torch's current stream (``self.stream``)."""
+
+    def __init__(self, nx, ny, nz, tau, kT, rho0=1.0, seed=0, scheme=FLBM_GMF,
+                 precision=FLBM_FP32, noise_rho0=False, stats_every=1, torch_memory=False,
+                 stream=None, noise_stream=0):
+        self.params = make_params(nx, ny, nz, tau, kT, rho0, seed, scheme, precision,
+                                  noise_rho0, stats_every, noise_stream)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.n = nx * ny * nz
+        self._h = C.c_void_p()
+        self._buf = None
+        self.stream = stream
+        dev, nbytes, sp = None, 0, None
+        if torch_memory:
+            import torch
+            nbytes = int(lib.flbm_state_bytes(C.byref(self.params)))
+            if nbytes == 0:
+                raise FlbmError(FLBM_E_INVALID, "invalid parameters")
+            self._buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            dev = self._buf.data_ptr()
+            if self.stream is None:
+                self.stream = torch.cuda.current_stream()
+        if self.stream is not None:
+            sp = self.stream.cuda_stream if hasattr(self.stream, "cuda_stream") else int(self.stream)
+        rc = lib.flbm_create_ex(C.byref(self.params), dev, nbytes, sp, C.byref(self._h))
+        if rc != FLBM_OK:
+            raise FlbmError(rc, lib.flbm_last_error(None).decode())
+
+    def close(self):
+        if self._h:
+            lib.flbm_destroy(self._h)
+            self._h = C.c_void_p()
+        self._buf = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Replica(_CtxOps):
+    """Borrowed context of one replica of an Ensemble (not destroyed here)."""
+
+    def __init__(self, ens: "Ensemble", index: int, params: flbm_params):
+        self._ens = ens            # keeps the ensemble alive
+        self.index = index
+        self.params = params
+        self.nx, self.ny, self.nz = params.nx, params.ny, params.nz
+        self.n = self.nx * self.ny * self.nz
+        self._h = C.c_void_p()
+        rc = lib.flbm_ensemble_replica(ens._e, int(index), C.byref(self._h))
+        if rc != FLBM_OK:
+            raise FlbmError(rc, lib.flbm_ensemble_last_error(ens._e).decode())
+
+
+class Ensemble:
+    """Owning wrapper of one flbm_ensemble: many replica boxes advanced by one
+    persistent kernel per step (see flbm_ensemble_create)."""
+
+    def __init__(self, params, stream=None):
+        self.params = list(params)
+        arr = (flbm_params * len(self.params))(*self.params)
+        self._e = C.c_void_p()
+        self.stream = stream
+        sp = None
+        if stream is not None:
+            sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        rc = lib.flbm_ensemble_create(arr, len(self.params), sp, C.byref(self._e))
+        if rc != FLBM_OK:
+            raise FlbmError(rc, lib.flbm_ensemble_last_error(None).decode())
+        self.replicas = [Replica(self, r, p) for r, p in enumerate(self.params)]
+        self.nodes = sum(r.n for r in self.replicas)
+
+    def _check(self, rc):
+        if rc != FLBM_OK:
+            raise FlbmError(rc, lib.flbm_ensemble_last_error(self._e).decode())
+
+    def __len__(self):
+        return len(self.replicas)
+
+    def __getitem__(self, i) -> Replica:
+        return self.replicas[i]
+
+    @property
+    def step_count(self) -> int:
+        return int(lib.flbm_ensemble_get_step(self._e))
+
+    def step(self, n: int = 1) -> None:
+        self._check(lib.flbm_ensemble_step(self._e, int(n)))
+
+    def graph(self, enable: bool = True) -> None:
+        self._check(lib.flbm_ensemble_graph(self._e, int(bool(enable))))
+
+    @property
+    def tuning(self) -> dict:
+        t = flbm_ensemble_tuning()
+        self._check(lib.flbm_ensemble_get_tuning(self._e, C.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, item_nodes=256, stages=2, compute_warps=8, ctas_per_sm=2) -> None:
+        t = flbm_ensemble_tuning(int(item_nodes), int(stages), int(compute_warps), int(ctas_per_sm), 0.0)
+        self._check(lib.flbm_ensemble_set_tuning(self._e, C.byref(t)))
+
+    def autotune(self, steps_per_trial: int = 4) -> dict:
+        t = flbm_ensemble_tuning()
+        self._check(lib.flbm_ensemble_autotune(self._e, int(steps_per_trial), C.byref(t)))
+        return t.as_dict()
+
+    def close(self):
+        if self._e:
+            for r in getattr(self, "replicas", []):
+                r._h = C.c_void_p()
+            lib.flbm_ensemble_destroy(self._e)
+            self._e = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

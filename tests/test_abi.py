@@ -85,6 +85,72 @@ def test_state_bytes_and_params(F):
     assert F.flbm_state_bytes(C.byref(p)) == 0
 
 
+def test_tuning_struct_layout(F, tmp_path):
+    src = tmp_path / "tl.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "flbm.h"
+int main(void) {
+  printf("%zu %zu\\n", sizeof(flbm_ensemble_tuning), offsetof(flbm_ensemble_tuning, ms_per_step));
+  return 0;
+}
+""")
+    exe = tmp_path / "tl"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+    assert vals == [C.sizeof(F.flbm_ensemble_tuning), F.flbm_ensemble_tuning.ms_per_step.offset]
+
+
+def _ens_params(F, n, changes):
+    ps = []
+    for r in range(n):
+        p = F.make_params(32, 4, 2, 0.8, 1e-5, seed=3, noise_stream=r)
+        for k, v in changes.get(r, {}).items():
+            setattr(p, k, v)
+        ps.append(p)
+    return ps
+
+
+@pytest.mark.parametrize("kw,count,code", [
+    ({1: dict(seed=4)}, 2, -1),             # one Philox key per ensemble
+    ({1: dict(noise_stream=0)}, 2, -1),     # streams must be distinct
+    ({0: dict(nx=48)}, 2, -1),              # nx multiple of 32
+    ({1: dict(scheme=0)}, 2, -1),
+    ({1: dict(stats_every=2)}, 2, -1),
+    ({0: dict(tau=0.5)}, 1, -1),
+    ({0: dict(noise_stream=1 << 24)}, 1, -1),
+    ({0: dict(nx=4096)}, 1, -1),            # two stages of 27 rows exceed shared memory
+    ({0: dict(precision=0), 1: dict(precision=0)}, 2, -6),
+    ({}, 0, -1),
+])
+def test_ensemble_validation_before_device(F, kw, count, code):
+    ps = _ens_params(F, max(count, 1), kw)
+    arr = (F.flbm_params * len(ps))(*ps)
+    e = C.c_void_p()
+    rc = F.flbm_ensemble_create(arr, count, None, C.byref(e))
+    assert rc == code
+    assert not e.value
+    assert F.flbm_ensemble_last_error(None)
+
+
+def test_noise_stream_is_validated(F):
+    p = F.make_params(8, 8, 8, 0.8, 1e-5, noise_stream=-1)
+    h = C.c_void_p()
+    assert F.flbm_create_ex(C.byref(p), None, 0, None, C.byref(h)) == -1
+    assert b"noise_stream" in F.flbm_last_error(None)
+
+
+def test_null_ensemble_calls_are_rejected(F):
+    assert F.flbm_ensemble_step(None, 1) == F.FLBM_E_INVALID
+    assert F.flbm_ensemble_count(None) == -1
+    assert F.flbm_ensemble_get_step(None) == -1
+    assert F.flbm_ensemble_graph(None, 1) == F.FLBM_E_INVALID
+    assert F.flbm_ensemble_autotune(None, 1, None) == F.FLBM_E_INVALID
+    F.flbm_ensemble_destroy(None)
+
+
 def test_null_context_calls_are_rejected(F):
     assert F.flbm_step(None, 1) == F.FLBM_E_INVALID
     assert F.flbm_get_step(None) == -1
