@@ -282,7 +282,8 @@ typedef struct flbm_ensemble_tuning {
                                rows * nx <= max(item_nodes, nx) */
     int32_t stages;         /* items in flight per CTA (shared-memory stages), 2..4 */
     int32_t compute_warps;  /* collision warps per CTA, 1..8 (plus one copy warp) */
-    int32_t ctas_per_sm;    /* resident CTAs per SM, >= 1 (capped by occupancy) */
+    int32_t ctas_per_sm;    /* resident CTAs per SM, >= 1; capped by occupancy, and
+                               flbm_ensemble_get_tuning reports the granted value */
     double ms_per_step;     /* flbm_ensemble_autotune: measured time of the shape;
                                otherwise 0 */
 } flbm_ensemble_tuning;

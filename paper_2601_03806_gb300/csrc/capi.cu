@@ -122,10 +122,19 @@ void fill_constants_t(const flbm_params &p, StepArgs<R> &a)
         k1 += 0xBB67AE85u;
     }
     a.ctr2 = uint32_t(p.noise_stream) << 8;
+    // the parts of Philox rounds 0 and 1 that depend only on the launch
+    // (counter words 1-3 = step lo, block | ctr2, step hi): round 0 maps word
+    // 2 to x0 = hi(M1 c2) ^ step lo ^ k0, y0 = lo(M1 c2); round 1 multiplies
+    // x0 by M0 (see philox4x32_10_r2)
+    const uint32_t step_lo = uint32_t(a.step), step_hi = uint32_t(a.step >> 32);
+    a.ph_zk = step_hi ^ a.rk[1];
     for (int b = 0; b < 6; ++b) {
-        const uint64_t m = uint64_t(0xCD9E8D57u) * (uint32_t(b) | a.ctr2);
-        a.c2hk[b] = uint32_t(m >> 32) ^ a.rk[0];
-        a.c2lo[b] = uint32_t(m);
+        const uint64_t p1 = uint64_t(0xCD9E8D57u) * (uint32_t(b) | a.ctr2);
+        const uint32_t x0 = uint32_t(p1 >> 32) ^ step_lo ^ a.rk[0];
+        const uint64_t q0 = uint64_t(0xD2511F53u) * x0;
+        a.ph_u1[b] = uint32_t(p1) ^ a.rk[2];
+        a.ph_u2[b] = uint32_t(q0 >> 32) ^ a.rk[3];
+        a.ph_u3[b] = uint32_t(q0);
     }
     a.noise_rho0 = p.noise_rho0;
     a.rho0 = R(p.rho0);

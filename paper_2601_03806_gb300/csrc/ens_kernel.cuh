@@ -46,14 +46,17 @@ struct EnsView {
     unsigned long long *bad_step;
 };
 
-// Round 0 of Philox counter word 2 (block | the replica's stream << 8),
-// computed per replica (the single-box kernels read it precomputed).
+// Philox block blk of node for a replica: round 0's product of counter word
+// 2 = blk | stream << 8 is formed here (philox4x32_10_r0).  Forming all
+// launch-uniform words of rounds 0-1 instead (as the single-box kernels read
+// them) lets the compiler hoist 19 values per item out of the node loop,
+// which spills at this kernel's register cap.
 template <typename R>
-__device__ __forceinline__ void ctr2_round0(const EnsView<R> &v, int blk, uint32_t &h2k, uint32_t &l2)
+__device__ __forceinline__ u32x4 noise_block(const EnsView<R> &v, uint32_t node, int blk)
 {
     const uint64_t m = uint64_t(0xCD9E8D57u) * (uint32_t(blk) | v.ctr2);
-    h2k = uint32_t(m >> 32) ^ v.rk[0];
-    l2 = uint32_t(m);
+    return philox4x32_10_r0(node, uint32_t(v.step), uint32_t(v.step >> 32), uint32_t(m >> 32) ^ v.rk[0],
+                            uint32_t(m), v.rk);
 }
 
 // Index of the replica holding global item i (replicas ordered by item0).
@@ -129,16 +132,17 @@ __device__ __forceinline__ int ens_pieces(const EnsReplica &r, uint32_t z, uint3
 }
 
 // Item i of replica rp: its plane z and first row y0.
+// (A replica has fewer than 2^31 nodes, so its item index fits 32 bits.)
 __device__ __forceinline__ void ens_item(const EnsReplica &rp, uint64_t i, uint32_t &z, uint32_t &y0)
 {
-    const uint64_t j = i - rp.item0;
-    z = uint32_t(j / rp.items_per_plane);
-    y0 = uint32_t(j - uint64_t(z) * rp.items_per_plane) * rp.rpi;
+    const uint32_t j = uint32_t(i - rp.item0);
+    z = j / rp.items_per_plane;
+    y0 = (j - z * rp.items_per_plane) * rp.rpi;
 }
 
-// 112 registers a thread: two CTAs of 8 + 1 warps fill the register file
-// (the same cap through __launch_bounds__(288, 2) left ptxas at 96, with
-// spills).
+// At most 112 registers a thread (the collision spills little at that cap).
+// Registers are split over the SM's four sub-partitions, so two CTAs fit an
+// SM up to 7 compute warps each; two CTAs of 8 + 1 warps would need <= 96.
 template <typename S, typename R, int SCHEME, bool ODD, bool STATS>
 __global__ void __maxnreg__(112) k_step_ens(const __grid_constant__ EnsArgs a)
 {
@@ -171,7 +175,7 @@ __global__ void __maxnreg__(112) k_step_ens(const __grid_constant__ EnsArgs a)
         const int d = int(lane);
         uint32_t r_load = r0, r_store = r0;
         bool ok = true;
-        auto move = [&](uint32_t k, uint32_t &cur, bool load, uint64_t *bar) {
+        auto move = [&](uint32_t k, uint32_t s, uint32_t &cur, bool load, uint64_t *bar) {
             const uint64_t i = begin + k;
             ens_advance(reps, a.nrep, i, cur);
             const EnsReplica &rp = reps[cur];
@@ -181,26 +185,30 @@ __global__ void __maxnreg__(112) k_step_ens(const __grid_constant__ EnsArgs a)
             uint32_t lo[2], cnt[2];
             const int np = ens_pieces<ODD>(rp, z, y0, d, go, lo, cnt);
             S *gp = static_cast<S *>(rp.g);
-            S *sp = stage + size_t(k % stages) * stage_elems + size_t(d) * stride;
+            S *sp = stage + size_t(s) * stage_elems + size_t(d) * stride;
             for (int q = 0; q < np; ++q) {
                 if (load) bulk_g2s(sp + lo[q], gp + go[q], cnt[q] * uint32_t(sizeof(S)), bar);
                 else bulk_s2g(gp + go[q], sp + lo[q], cnt[q] * uint32_t(sizeof(S)));
             }
         };
+        // stage and mbarrier phase of the next store (ss, sph) and load (s)
+        uint32_t ss = 0, sph = 0;
         auto store_item = [&](uint32_t kk) {
-            const uint32_t s = kk % stages;
-            ok = mbar_wait(&empty[s], (kk / stages) & 1u);
+            ok = mbar_wait(&empty[ss], sph);
             if (!ok) return;
             if (d < kQ) {
-                move(kk, r_store, false, nullptr);
+                move(kk, ss, r_store, false, nullptr);
                 bulk_commit();
                 bulk_wait_read_all();
             }
             __syncwarp();
+            if (++ss == stages) {
+                ss = 0;
+                sph ^= 1u;
+            }
         };
-        uint32_t k = 0;
+        uint32_t k = 0, s = 0;
         for (; k < nk; ++k) {
-            const uint32_t s = k % stages;
             if (k >= stages) {
                 store_item(k - stages);
                 if (!ok) break;
@@ -212,7 +220,8 @@ __global__ void __maxnreg__(112) k_step_ens(const __grid_constant__ EnsArgs a)
                                                     a.tx_pad);
             }
             __syncwarp();
-            if (d < kQ) move(k, r_load, true, &full[s]);
+            if (d < kQ) move(k, s, r_load, true, &full[s]);
+            if (++s == stages) s = 0;
         }
         for (uint32_t kk = (k > stages ? k - stages : 0); ok && kk < k; ++kk) store_item(kk);
         if (!ok && lane == 0) atomicOr(a.flag, 2u);
@@ -225,6 +234,7 @@ __global__ void __maxnreg__(112) k_step_ens(const __grid_constant__ EnsArgs a)
 #pragma unroll
         for (int s = 0; s < NSTAT; ++s) acc[s] = R(0);
         uint32_t r = r0;
+        uint32_t s = 0, ph = 0;   // stage and mbarrier phase of item k
         for (uint32_t k = 0; k < nk; ++k) {
             const uint64_t i = begin + k;
             ens_advance(reps, a.nrep, i, r);
@@ -235,17 +245,20 @@ __global__ void __maxnreg__(112) k_step_ens(const __grid_constant__ EnsArgs a)
             uint32_t z, y0;
             ens_item(rp, i, z, y0);
             const uint32_t base = (z * rp.ny + y0) * nx;   // first node of the item
-            const uint32_t s = k % stages;
+            // row of local node l: (l + 1/2) / nx in FP32 is within 128 x 2^-23
+            // of its exact value and at least 1/(2 nx) >= 5.6e-4 from an
+            // integer (l < 4096, nx <= 896), so truncation gives l / nx exactly
+            const float inv_nx = __frcp_rn(float(nx));
             R nz[kNoise];
             if (threadIdx.x < item_nodes) draw_noise(v, base + threadIdx.x, nz);
-            if (!mbar_wait(&full[s], (k / stages) & 1u)) {
+            if (!mbar_wait(&full[s], ph)) {
                 if (lane == 0) atomicOr(a.flag, 2u);
                 break;
             }
             S *st = stage + size_t(s) * stage_elems;
             for (uint32_t l = threadIdx.x; l < item_nodes; l += nc) {
                 if (l != threadIdx.x) draw_noise(v, base + l, nz);
-                const uint32_t t = l / nx, x = l - t * nx, rb = t * nx;
+                const uint32_t t = uint32_t((float(l) + 0.5f) * inv_nx), x = l - t * nx, rb = t * nx;
                 const uint32_t xsh[3] = {rb + (x ? x - 1 : nx - 1), l, rb + ((x + 1 < nx) ? x + 1 : 0)};
                 R vv[3][3][3];
 #pragma unroll
@@ -272,6 +285,10 @@ __global__ void __maxnreg__(112) k_step_ens(const __grid_constant__ EnsArgs a)
             fence_proxy_async_smem();   // generic-proxy writes before the bulk store reads
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
+            if (++s == stages) {
+                s = 0;
+                ph ^= 1u;
+            }
             if (STATS) {
                 const bool leaving = (k + 1 == nk) || (r + 1 < a.nrep && reps[r + 1].item0 <= i + 1);
                 if (leaving) {

@@ -176,6 +176,7 @@ int apply_tuning(flbm_ensemble *e, const flbm_ensemble_tuning &t)
     e->args.nitems = nitems;
     e->args.partials = e->partials;
     e->tune = t;
+    e->tune.ctas_per_sm = per_sm;      // what the device grants, not what was asked
     e->tune.ms_per_step = 0.0;
     e->grid = grid;
     e->threads = threads;

@@ -35,8 +35,10 @@ struct StepArgs {
     uint64_t step;                // t of this collision (noise counter)
     uint32_t rk[20];              // Philox round keys (k0, k1) of rounds 0..9
     uint32_t ctr2;                // noise stream id << 8 (Philox counter word 2 = block | ctr2)
-    uint32_t c2hk[6], c2lo[6];    // Philox round 0 of word 2 = block | ctr2 for blocks 0..5:
-                                  // hi(M1 (block | ctr2)) ^ rk[0] and lo(M1 (block | ctr2))
+    // Philox rounds 0-1 of the launch-uniform counter words (step, block |
+    // ctr2) for blocks 0..5, precomputed on the host (philox4x32_10_r2)
+    uint32_t ph_zk;               // step hi ^ rk[1]
+    uint32_t ph_u1[6], ph_u2[6], ph_u3[6];
     int32_t noise_rho0;           // phi_k uses rho0 instead of rho(x,t)
     uint32_t tx_pad;              // failure injection: bytes the row pipeline
                                   // expects beyond what it copies (0 normally)

@@ -155,10 +155,9 @@ __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, const uint32_t (&rk)[20]
     return c;
 }
 
-// The same block function with round 0's product of counter word 2 supplied
-// by the caller: h2k = hi(0xCD9E8D57 * c.z) ^ rk[0], l2 = lo(0xCD9E8D57 * c.z).
-// When c.z is uniform over a launch (block index | stream << 8) the host
-// computes the pair once, and the kernel reads it as a constant.
+// The block function with round 0's product of counter word 2 supplied by
+// the caller (h2k = hi(M1 c2) ^ k0(0), l2 = lo(M1 c2)) and rounds 1..9 as
+// usual: for callers whose c2 is uniform but not known to the host.
 __device__ __forceinline__ u32x4 philox4x32_10_r0(uint32_t c0, uint32_t c1, uint32_t c3, uint32_t h2k,
                                                   uint32_t l2, const uint32_t (&rk)[20])
 {
@@ -166,6 +165,30 @@ __device__ __forceinline__ u32x4 philox4x32_10_r0(uint32_t c0, uint32_t c1, uint
     u32x4 c{h2k ^ c1, l2, uint32_t(p0 >> 32) ^ c3 ^ rk[1], uint32_t(p0)};
 #pragma unroll
     for (int r = 1; r < 10; ++r) {
+        const uint64_t q0 = uint64_t(0xD2511F53u) * c.x;
+        const uint64_t q1 = uint64_t(0xCD9E8D57u) * c.z;
+        c = u32x4{uint32_t(q1 >> 32) ^ c.y ^ rk[2 * r], uint32_t(q1),
+                  uint32_t(q0 >> 32) ^ c.w ^ rk[2 * r + 1], uint32_t(q0)};
+    }
+    return c;
+}
+
+// The same block function for counter (c0, c1, c2, c3) when only c0 varies
+// between the threads of a launch.  Rounds 0 and 1 then split into a part
+// that depends on c0 alone and launch-uniform words the caller supplies:
+//   zk = c3 ^ k1(0);  x0 = hi(M1 c2) ^ c1 ^ k0(0),  y0 = lo(M1 c2);
+//   u1 = y0 ^ k0(1),  u2 = hi(M0 x0) ^ k1(1),  u3 = lo(M0 x0).
+// Round 0 gives (x0, y0, hi(M0 c0) ^ zk, lo(M0 c0)) and round 1
+// (hi(M1 z0) ^ u1, lo(M1 z0), u2 ^ w0, u3); rounds 2..9 follow as usual.
+__device__ __forceinline__ u32x4 philox4x32_10_r2(uint32_t c0, uint32_t zk, uint32_t u1, uint32_t u2,
+                                                  uint32_t u3, const uint32_t (&rk)[20])
+{
+    const uint64_t p0 = uint64_t(0xD2511F53u) * c0;
+    const uint32_t z0 = uint32_t(p0 >> 32) ^ zk, w0 = uint32_t(p0);
+    const uint64_t p1 = uint64_t(0xCD9E8D57u) * z0;
+    u32x4 c{uint32_t(p1 >> 32) ^ u1, uint32_t(p1), u2 ^ w0, u3};
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
         const uint64_t q0 = uint64_t(0xD2511F53u) * c.x;
         const uint64_t q1 = uint64_t(0xCD9E8D57u) * c.z;
         c = u32x4{uint32_t(q1 >> 32) ^ c.y ^ rk[2 * r], uint32_t(q1),

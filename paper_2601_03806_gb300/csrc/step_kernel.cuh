@@ -157,20 +157,13 @@ __device__ __forceinline__ void block_reduce_store(const R (&acc)[NSTAT], double
 constexpr int kNoise = kQ - 4;
 
 // Philox block blk of node at the step: counter (node, step lo, blk | stream
-// << 8, step hi).  ctr2_round0 supplies round 0's product of counter word 2:
-// host-precomputed kernel constants for one box; per replica in an ensemble.
+// << 8, step hi).  One box: the launch-uniform words of rounds 0-1 come
+// precomputed from the host (philox4x32_10_r2).  An ensemble replica has its
+// own overload (ens_kernel.cuh).
 template <typename R>
-__device__ __forceinline__ void ctr2_round0(const StepArgs<R> &a, int blk, uint32_t &h2k, uint32_t &l2)
+__device__ __forceinline__ u32x4 noise_block(const StepArgs<R> &a, uint32_t node, int blk)
 {
-    h2k = a.c2hk[blk];
-    l2 = a.c2lo[blk];
-}
-template <typename A>
-__device__ __forceinline__ u32x4 noise_block(const A &a, uint32_t node, int blk)
-{
-    uint32_t h2k, l2;
-    ctr2_round0(a, blk, h2k, l2);
-    return philox4x32_10_r0(node, uint32_t(a.step), uint32_t(a.step >> 32), h2k, l2, a.rk);
+    return philox4x32_10_r2(node, a.ph_zk, a.ph_u1[blk], a.ph_u2[blk], a.ph_u3[blk], a.rk);
 }
 
 // A is the step's scalar set: StepArgs<R> for one box, or a per-replica view
