@@ -37,6 +37,9 @@ BYTES_PER_NODE = {"fp32": 27 * 4 * 2, "fp16": 27 * 2 * 2, "fp64": 27 * 8 * 2}
 CS2 = 1.0 / 3.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_rows_f32_gmf_traffic.txt")
 KERNEL_SOURCES = ["step_kernel.cuh", "lattice.cuh", "internal.h", "step_f32.cu"]
+ENS_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_ens_f32_gmf_traffic.txt")
+ENS_KERNEL_SOURCES = ["ens_kernel.cuh", "step_kernel.cuh", "lattice.cuh", "internal.h", "stats.cuh",
+                      "ens_f32.cu"]
 
 
 def parse_args(argv=None):
@@ -180,24 +183,24 @@ def measured_hbm_peak():
         return 6800.0, "of fallback"
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=None) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in (KERNEL_SOURCES if sources is None else sources):
         with open(os.path.join(ROOT, "paper_2601_03806_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(nodes: int):
+def recorded_traffic(nodes: int, path=None, sources=None):
     """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
     scaled to the box size; None if the kernel changed since the capture."""
     try:
         kv = {}
-        for ln in open(TRAFFIC_FILE):
+        for ln in open(TRAFFIC_FILE if path is None else path):
             if ":" in ln and not ln.startswith("#"):
                 k, v = ln.split(":", 1)
                 kv[k.strip()] = v.strip()
-        if kv.get("kernel_source_hash") != kernel_source_hash():
+        if kv.get("kernel_source_hash") != kernel_source_hash(sources):
             return None
         per_node = float(kv["dram_bytes_per_node"])
         return per_node * nodes
@@ -519,7 +522,8 @@ def run_ensemble(args, rank, local, ws):
     peak, peak_src = measured_hbm_peak()
     achieved = BYTES_PER_NODE["fp32"] * N / (step_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": recorded_traffic(N, ENS_TRAFFIC_FILE, ENS_KERNEL_SOURCES),
                 "kernel": "flbm::k_step_ens<float,float,GMF,*,stats> + flbm::k_ens_post (per-step "
                           "time of both, graph replay)",
                 "kernel_ms": step_ms, "algorithmic_bytes_per_launch": BYTES_PER_NODE["fp32"] * N}
