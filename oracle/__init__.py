@@ -18,5 +18,10 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
                         its full-order equilibrium coefficients are pinned against
                         the product-form D3Q27 equilibrium
 * ``structure_factor``  pinned: numpy FFT, Parseval, single-plane-wave shell
+* ``mlp`` (learned collision): forward/backward pinned by central finite
+                        differences and closed forms, the projection by the
+                        conservation identities, the training target by the
+                        closed-form ghost synthesis; the target inherits the
+                        Reg-FLBM reading (parity unpinned against the paper)
 """
 from .oracle import *  # noqa: F401,F403
