@@ -341,6 +341,33 @@ const char *flbm_ensemble_last_error(const flbm_ensemble *e);
 /* Release the ensemble and its replica contexts (not a caller stream). */
 void flbm_ensemble_destroy(flbm_ensemble *e);
 
+/* ------------------------------------------------------------------------
+ * Learned collision: a per-node network that corrects the GMF collision
+ * towards the regularized collision (Reg-FLBM, Sec. III).  The paper has no
+ * network; this is the library's.
+ *
+ *   x   28 features: the pre-collision deviations g_i = f_i - w_i rho0 in
+ *       units of sqrt(rho0 kT w_i / c_s^2) (i = 0..26, ABI velocity order),
+ *       and omega - 1;
+ *   y   = W3 h2 + b3, h2 = silu(W2 h1 + b2), h1 = silu(W1 x + b1)
+ *       (28-64-64-27, silu(z) = z / (1 + e^-z));
+ *   the step adds P(w_i sigma^3 y_i), sigma = sqrt(kT / rho0), to the GMF
+ *   post-collision populations, P removing mass and momentum exactly:
+ *   P(d)_i = d_i - w_i (sum_j d_j + c_i . sum_j d_j c_j / c_s^2).
+ *
+ * Parameters: FLBM_MLP_NPARAM floats in the order W1[64][28], b1[64],
+ * W2[64][64], b2[64], W3[27][64], b3[27] (row-major, W[out][in]).  The
+ * tensor-core path rounds the weights, the features and both hidden
+ * activations to bfloat16 (nearest, ties to even) and accumulates in FP32
+ * in tensor memory; the biases stay FP32. */
+#define FLBM_MLP_NPARAM 7771
+
+/* Network outputs y[n][27] of features x[n][28] (host arrays), evaluated
+ * by the tcgen05 tensor-core kernel the learned step uses.  Allocates and
+ * frees its own device buffers; synchronous.  Errors via
+ * flbm_last_error(NULL). */
+int flbm_mlp_infer(const float *params, const float *x, int64_t n, float *y);
+
 #ifdef __cplusplus
 }
 #endif

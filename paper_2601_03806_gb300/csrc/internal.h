@@ -150,6 +150,15 @@ void fill_step_constants(const flbm_params &p, StepArgs<float> &a);
 void fill_step_constants(const flbm_params &p, StepArgs<double> &a);
 // Set the calling thread's error text returned by flbm_last_error(NULL).
 void set_thread_error(const char *msg);
+}  // namespace flbm
+
+#include <vector>
+
+namespace flbm {
+// Learned-collision network: the bf16 weight image + FP32 biases in the
+// tensor-core operand layout (mlp_infer.cu) from the flat FP32 parameter
+// vector of include/flbm.h (FLBM_MLP_NPARAM values).
+void build_mlp_image(const float *params, std::vector<unsigned char> &img);
 
 // Auxiliary kernels (aux.cu).  `prec` is 0 (double storage), 1 (float) or
 // 2 (half).

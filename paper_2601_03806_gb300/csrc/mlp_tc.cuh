@@ -1,0 +1,211 @@
+// mlp_tc.cuh -- the learned-collision network (28-64-64-27, SiLU, BF16
+// weights, FP32 accumulation) on the tcgen05 tensor cores, one tile of 128
+// nodes per CTA at a time.
+//
+// A CTA of 128 threads: thread t owns tile row t (one node).  Per tile
+//   A1[128 x 32]  bf16 features (28 + 4 zero columns)      -> shared memory
+//   D1 = A1 W1^T  (M 128, N 64, K 32: two MMAs)             -> tensor memory cols 0..63
+//   h1 = silu(D1 + b1) as bf16                               -> A2 (shared)
+//   D2 = h1 W2^T  (N 64, K 64: four MMAs)                    -> cols 64..127
+//   h2 = silu(D2 + b2) as bf16                               -> A2 again
+//   D3 = h2 W3^T  (N 32, K 64: four MMAs; rows 27..31 of W3 are zero) -> cols 0..31
+//   y = D3 + b3                                              -> thread t's registers
+// One elected thread issues the MMAs; their completion arrives on an
+// mbarrier that every thread waits on (bounded).  The weight image (bf16,
+// already in the operand layout of umma.cuh) and the FP32 biases are copied
+// into shared memory once per CTA.  128 tensor-memory columns per CTA; the
+// shared-memory footprint keeps at most 4 CTAs on an SM, so the 512 columns
+// of an SM are never over-subscribed.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "step_kernel.cuh"
+#include "umma.cuh"
+
+namespace flbm {
+
+constexpr int kMlpIn = 28, kMlpHidden = 64, kMlpOut = 27;
+constexpr uint32_t kSbo32 = 4 * 128;          // SBO of a K = 32 operand
+constexpr uint32_t kSbo64 = 8 * 128;          // SBO of a K = 64 operand
+constexpr uint32_t kW1Off = 0, kW2Off = 4096, kW3Off = 12288, kBiasOff = 16384;
+constexpr uint32_t kMlpImageBytes = kBiasOff + (64 + 64 + 32) * 4;   // 17,024 B
+constexpr uint32_t kMlpTmemCols = 128;
+constexpr size_t kMlpSmemBytes = 47 * 1024;   // >= sizeof(MlpSmem); <= 4 CTAs per SM
+
+struct MlpSmem {
+    __align__(128) unsigned char w[kBiasOff];          // W1 | W2 | W3 bf16 images
+    float bias[64 + 64 + 32];                          // b1 | b2 | b3 (b3 zero-padded)
+    __align__(128) unsigned char a1[128 * 32 * 2];
+    __align__(128) unsigned char a2[128 * 64 * 2];
+    uint64_t bar;
+    uint32_t tmem;
+};
+static_assert(sizeof(MlpSmem) <= kMlpSmemBytes, "MlpSmem exceeds its shared-memory budget");
+
+// silu(z) = z sigmoid(z) = 0.5 z (1 + tanh(z / 2)), with the hardware tanh
+// (absolute error about 2^-11, below the bf16 rounding of the activations).
+__device__ __forceinline__ float silu_fast(float z)
+{
+    float t;
+    asm("tanh.approx.f32 %0, %1;\n" : "=f"(t) : "f"(0.5f * z));
+    const float hz = 0.5f * z;
+    return __fmaf_rn(hz, t, hz);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// Write 16 consecutive columns k0..k0+15 of row r of a K-major operand.
+__device__ __forceinline__ void store_row16(unsigned char *base, uint32_t sbo, uint32_t r, uint32_t k0,
+                                            const float (&v)[16])
+{
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        uint4 q;
+        q.x = pack_bf16x2(v[8 * half + 0], v[8 * half + 1]);
+        q.y = pack_bf16x2(v[8 * half + 2], v[8 * half + 3]);
+        q.z = pack_bf16x2(v[8 * half + 4], v[8 * half + 5]);
+        q.w = pack_bf16x2(v[8 * half + 6], v[8 * half + 7]);
+        *reinterpret_cast<uint4 *>(base + core_offset(r, k0 + 8 * half, sbo)) = q;
+    }
+}
+
+// CTA set-up: weight image to shared memory, mbarrier, tensor memory.
+__device__ __forceinline__ void mlp_setup(MlpSmem &sm, const unsigned char *__restrict__ img)
+{
+    const uint4 *src = reinterpret_cast<const uint4 *>(img);
+    uint4 *dst = reinterpret_cast<uint4 *>(sm.w);
+    for (uint32_t i = threadIdx.x; i < kBiasOff / 16; i += blockDim.x) dst[i] = src[i];
+    const float *bsrc = reinterpret_cast<const float *>(img + kBiasOff);
+    for (uint32_t i = threadIdx.x; i < 160; i += blockDim.x) sm.bias[i] = bsrc[i];
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bar, 1);
+        mbar_init_fence();
+    }
+    if (threadIdx.x < 32) tmem_alloc(&sm.tmem, kMlpTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+// CTA tear-down: every tensor-memory read done, then free the columns.
+__device__ __forceinline__ void mlp_teardown(MlpSmem &sm)
+{
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(sm.tmem, kMlpTmemCols);
+}
+
+// Wait for the MMAs committed to sm.bar; the outcome is made uniform over the
+// CTA so that no thread leaves the tile loop alone.
+__device__ __forceinline__ bool mlp_wait(MlpSmem &sm, uint32_t &phase)
+{
+    const bool ok = mbar_wait(&sm.bar, phase);
+    phase ^= 1u;
+    const bool all = __syncthreads_and(ok) != 0;
+    tc_fence_after();
+    return all;
+}
+
+__device__ __forceinline__ void mlp_sync_for_mma()
+{
+    fence_proxy_async_smem();   // generic-proxy operand writes before the MMAs read them
+    tc_fence_before();          // earlier tensor-memory reads before the MMAs overwrite
+    __syncthreads();
+}
+
+// One tile: x = this thread's 28 features (row threadIdx.x), y = its 27
+// outputs.  work() runs while the first layer's MMAs are in flight.  Returns
+// false (on every thread) if a wait ran out; the MMAs are then drained with
+// one more bounded wait before returning.
+template <typename Work>
+__device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const float (&x)[kMlpIn],
+                                         float (&y)[kMlpOut], Work &&work)
+{
+    const uint32_t t = threadIdx.x;
+    const uint32_t tmem = sm.tmem;
+    const uint32_t lane_base = (t & ~31u) << 16;
+    const uint32_t w = smem_u32(sm.w), a1 = smem_u32(sm.a1), a2 = smem_u32(sm.a2);
+    constexpr uint32_t idesc64 = umma_idesc_bf16(128, 64), idesc32 = umma_idesc_bf16(128, 32);
+    {
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = x[i];
+        store_row16(sm.a1, kSbo32, t, 0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = (16 + i < kMlpIn) ? x[16 + i] : 0.0f;
+        store_row16(sm.a1, kSbo32, t, 16, v);
+    }
+    mlp_sync_for_mma();
+    if (t == 0) {
+        tc_fence_after();
+#pragma unroll
+        for (uint32_t s = 0; s < 2; ++s)
+            umma_bf16(tmem, umma_smem_desc(a1 + 256 * s, 128, kSbo32),
+                      umma_smem_desc(w + kW1Off + 256 * s, 128, kSbo32), idesc64, s > 0);
+        umma_commit(&sm.bar);
+    }
+    work();
+    bool ok = mlp_wait(sm, phase);
+    if (ok) {
+#pragma unroll
+        for (uint32_t ch = 0; ch < 4; ++ch) {
+            float z[16];
+            tmem_ld16(tmem + lane_base + 16 * ch, z);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) z[i] = silu_fast(z[i] + sm.bias[16 * ch + i]);
+            store_row16(sm.a2, kSbo64, t, 16 * ch, z);
+        }
+        mlp_sync_for_mma();
+        if (t == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (uint32_t s = 0; s < 4; ++s)
+                umma_bf16(tmem + 64, umma_smem_desc(a2 + 256 * s, 128, kSbo64),
+                          umma_smem_desc(w + kW2Off + 256 * s, 128, kSbo64), idesc64, s > 0);
+            umma_commit(&sm.bar);
+        }
+        ok = mlp_wait(sm, phase);
+    }
+    if (ok) {
+#pragma unroll
+        for (uint32_t ch = 0; ch < 4; ++ch) {
+            float z[16];
+            tmem_ld16(tmem + lane_base + 64 + 16 * ch, z);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) z[i] = silu_fast(z[i] + sm.bias[64 + 16 * ch + i]);
+            store_row16(sm.a2, kSbo64, t, 16 * ch, z);
+        }
+        mlp_sync_for_mma();
+        if (t == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (uint32_t s = 0; s < 4; ++s)
+                umma_bf16(tmem, umma_smem_desc(a2 + 256 * s, 128, kSbo64),
+                          umma_smem_desc(w + kW3Off + 256 * s, 128, kSbo64), idesc32, s > 0);
+            umma_commit(&sm.bar);
+        }
+        ok = mlp_wait(sm, phase);
+    }
+    if (ok) {
+#pragma unroll
+        for (uint32_t ch = 0; ch < 2; ++ch) {
+            float z[16];
+            tmem_ld16(tmem + lane_base + 16 * ch, z);
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (16 * ch + i < kMlpOut) y[16 * ch + i] = z[i] + sm.bias[128 + 16 * ch + i];
+        }
+        return true;
+    }
+    // a wait ran out: give the MMAs in flight one more bounded wait
+    mbar_wait(&sm.bar, phase);
+    return false;
+}
+
+}  // namespace flbm

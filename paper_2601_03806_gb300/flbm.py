@@ -103,6 +103,7 @@ def _load():
         "flbm_ensemble_get_step": ([vp], i64),
         "flbm_ensemble_last_error": ([vp], C.c_char_p),
         "flbm_ensemble_destroy": ([vp], None),
+        "flbm_mlp_infer": ([vp, vp, i64, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -148,6 +149,21 @@ flbm_ensemble_count = lib.flbm_ensemble_count
 flbm_ensemble_get_step = lib.flbm_ensemble_get_step
 flbm_ensemble_last_error = lib.flbm_ensemble_last_error
 flbm_ensemble_destroy = lib.flbm_ensemble_destroy
+flbm_mlp_infer = lib.flbm_mlp_infer
+MLP_NPARAM = 7771
+
+
+def mlp_infer(params, x) -> np.ndarray:
+    """Network outputs y[n, 27] of features x[n, 28] on the tensor cores."""
+    p = np.ascontiguousarray(params, np.float32)
+    if p.size != MLP_NPARAM:
+        raise ValueError("params must hold %d values" % MLP_NPARAM)
+    xx = np.ascontiguousarray(x, np.float32).reshape(-1, 28)
+    y = np.empty((xx.shape[0], 27), np.float32)
+    rc = lib.flbm_mlp_infer(_ptr(p), _ptr(xx), xx.shape[0], _ptr(y))
+    if rc != FLBM_OK:
+        raise FlbmError(rc, lib.flbm_last_error(None).decode())
+    return y
 
 
 def _ptr(a: np.ndarray):
