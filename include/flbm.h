@@ -368,6 +368,35 @@ void flbm_ensemble_destroy(flbm_ensemble *e);
  * flbm_last_error(NULL). */
 int flbm_mlp_infer(const float *params, const float *x, int64_t n, float *y);
 
+/* Training pairs of every node of the context's current state, written to
+ * caller-owned device arrays: dev_x[N][28] features (as above, with the
+ * context's rho0, kT, tau) and dev_t[N][27] targets
+ *   t_i = w_i sum_{k >= 10} e_ki rho u^(deg k) / b_k / (w_i sigma^3),
+ * the ghost equilibrium content by which the regularized collision
+ * (Reg-FLBM, this library's reading: unit ghost relaxation towards the
+ * full-order equilibrium) differs from the GMF collision of the same
+ * pre-collision state, in units of the network output.  Computed in FP64,
+ * stored as FP32.  Needs kT > 0.  Node n = x + nx (y + ny z). */
+int flbm_mlp_pairs(flbm_ctx *c, float *dev_x, float *dev_t);
+
+/* Gradient of L = mean over the n samples and 27 outputs of (y - t)^2 with
+ * respect to the FLBM_MLP_NPARAM parameters (FP32 forward and backward on
+ * the CUDA cores, exact silu, FP64 sums over samples in a fixed order):
+ * dev_x[n][28], dev_t[n][27] device arrays, grad[FLBM_MLP_NPARAM] and *loss
+ * (may be NULL) host outputs.  1 <= n < 2^32.  Errors via
+ * flbm_last_error(NULL). */
+int flbm_mlp_grad(const float *params, const float *dev_x, const float *dev_t, int64_t n, float *grad,
+                  double *loss);
+
+/* Adam training of params (host, in place) on n device samples: `epochs`
+ * passes, each over all samples in a fresh order (an affine bijection of
+ * [0, n) drawn from seed), in mini-batches of `batch`; step size lr with a
+ * cosine decay to 5 % over the run; beta1 0.9, beta2 0.999, eps 1e-8.
+ * epoch_loss[epochs] (may be NULL) receives each epoch's mean loss over its
+ * mini-batches (measured before each update). */
+int flbm_mlp_train(float *params, const float *dev_x, const float *dev_t, int64_t n, int epochs, int batch,
+                   double lr, uint64_t seed, double *epoch_loss);
+
 #ifdef __cplusplus
 }
 #endif

@@ -701,6 +701,25 @@ int flbm_set_state(flbm_ctx *c, const void *host)
     return state_replaced(c);
 }
 
+int flbm_mlp_pairs(flbm_ctx *c, float *dev_x, float *dev_t)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (!dev_x || !dev_t) return fail(c, FLBM_E_INVALID, "dev_x and dev_t must not be NULL");
+    if (!(c->p.kT > 0.0)) return fail(c, FLBM_E_INVALID, "training pairs need kT > 0 (the feature scale)");
+    int rc = ensure_pipe(c);
+    if (rc) return rc;
+    const BoxDesc b = box_of(c);
+    const int prec = prec_code(c);
+    for (uint64_t n0 = 0; n0 < c->n; n0 += c->pipe_nodes) {
+        const uint64_t cn = std::min<uint64_t>(c->pipe_nodes, c->n - n0);
+        CK(c, launch_gather_f(c->g, prec, b, n0, cn, c->pipe[0], true, c->stream));
+        CK(c, launch_mlp_pairs(c->pipe[0], cn, c->p.rho0, c->p.kT, 1.0 / c->p.tau, dev_x + n0 * 28,
+                               dev_t + n0 * 27, c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLBM_OK;
+}
+
 int flbm_timing_enable(flbm_ctx *c, int enable)
 {
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");

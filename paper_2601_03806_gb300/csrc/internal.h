@@ -159,6 +159,10 @@ namespace flbm {
 // tensor-core operand layout (mlp_infer.cu) from the flat FP32 parameter
 // vector of include/flbm.h (FLBM_MLP_NPARAM values).
 void build_mlp_image(const float *params, std::vector<unsigned char> &img);
+// Training pairs (mlp_train.cu) of cn nodes from FP64 deviations g[27][cn]:
+// features X[cn][28] and targets T[cn][27] (device arrays).
+cudaError_t launch_mlp_pairs(const double *g, uint64_t cn, double rho0, double kT, double omega, float *X,
+                             float *T, cudaStream_t s);
 
 // Auxiliary kernels (aux.cu).  `prec` is 0 (double storage), 1 (float) or
 // 2 (half).

@@ -104,6 +104,9 @@ def _load():
         "flbm_ensemble_last_error": ([vp], C.c_char_p),
         "flbm_ensemble_destroy": ([vp], None),
         "flbm_mlp_infer": ([vp, vp, i64, vp], i32),
+        "flbm_mlp_pairs": ([vp, vp, vp], i32),
+        "flbm_mlp_grad": ([vp, vp, vp, i64, vp, vp], i32),
+        "flbm_mlp_train": ([vp, vp, vp, i64, i32, i32, d, u64, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -150,7 +153,40 @@ flbm_ensemble_get_step = lib.flbm_ensemble_get_step
 flbm_ensemble_last_error = lib.flbm_ensemble_last_error
 flbm_ensemble_destroy = lib.flbm_ensemble_destroy
 flbm_mlp_infer = lib.flbm_mlp_infer
+flbm_mlp_pairs = lib.flbm_mlp_pairs
+flbm_mlp_grad = lib.flbm_mlp_grad
+flbm_mlp_train = lib.flbm_mlp_train
 MLP_NPARAM = 7771
+
+
+def _dev(t):
+    """Device address of a CUDA torch tensor (float32, contiguous)."""
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def mlp_grad(params, dev_x, dev_t):
+    """(gradient[7771], loss) of the mean squared error on device samples."""
+    p = np.ascontiguousarray(params, np.float32)
+    g = np.empty(MLP_NPARAM, np.float32)
+    loss = C.c_double()
+    n = dev_x.shape[0]
+    rc = lib.flbm_mlp_grad(_ptr(p), _dev(dev_x), _dev(dev_t), n, _ptr(g), C.byref(loss))
+    if rc != FLBM_OK:
+        raise FlbmError(rc, lib.flbm_last_error(None).decode())
+    return g, loss.value
+
+
+def mlp_train(params, dev_x, dev_t, epochs, batch=1024, lr=3e-3, seed=0):
+    """Adam-trained copy of params and the per-epoch mean losses."""
+    p = np.array(params, np.float32)
+    losses = np.zeros(int(epochs))
+    rc = lib.flbm_mlp_train(_ptr(p), _dev(dev_x), _dev(dev_t), dev_x.shape[0], int(epochs), int(batch),
+                            float(lr), int(seed), _ptr(losses))
+    if rc != FLBM_OK:
+        raise FlbmError(rc, lib.flbm_last_error(None).decode())
+    return p, losses
 
 
 def mlp_infer(params, x) -> np.ndarray:
@@ -228,6 +264,10 @@ class _CtxOps:
 
     def stats_reset(self) -> None:
         self._check(lib.flbm_stats_reset(self._h))
+
+    def mlp_pairs(self, dev_x, dev_t) -> None:
+        """Training pairs of every node into CUDA tensors x[N, 28], t[N, 27]."""
+        self._check(lib.flbm_mlp_pairs(self._h, _dev(dev_x), _dev(dev_t)))
 
     def structure_factor(self, observable: int, nshell: int):
         S = np.zeros(nshell)
