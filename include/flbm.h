@@ -53,8 +53,11 @@ extern "C" {
 
 typedef struct flbm_ctx flbm_ctx; /* opaque, owned by the library */
 
-/* Collision scheme (Sec. III compares all three). */
-enum flbm_scheme { FLBM_BGK = 0, FLBM_GMF = 1, FLBM_REG = 2 };
+/* Collision scheme (Sec. III compares the first three).  FLBM_LEARNED is
+ * this library's: GMF-FLBM plus a trained network's correction towards
+ * Reg-FLBM (see "Learned collision" below); FP32 storage, kT > 0, and the
+ * network set with flbm_set_mlp before the first step. */
+enum flbm_scheme { FLBM_BGK = 0, FLBM_GMF = 1, FLBM_REG = 2, FLBM_LEARNED = 3 };
 
 /* Storage precision of the populations.
  * FLBM_FP64: deviations g_i = f_i - w_i rho0 in double, FP64 arithmetic.
@@ -396,6 +399,13 @@ int flbm_mlp_grad(const float *params, const float *dev_x, const float *dev_t, i
  * mini-batches (measured before each update). */
 int flbm_mlp_train(float *params, const float *dev_x, const float *dev_t, int64_t n, int epochs, int batch,
                    double lr, uint64_t seed, double *epoch_loss);
+
+/* Network of a FLBM_LEARNED context (FLBM_MLP_NPARAM floats, copied; may be
+ * replaced between steps).  Each step then collides every node with the GMF
+ * collision (noise included) and adds P(w_i sigma^3 y_i(x)) computed on the
+ * tensor cores from the node's pre-collision features.  FLBM_E_INVALID for
+ * other schemes. */
+int flbm_set_mlp(flbm_ctx *c, const float *params);
 
 #ifdef __cplusplus
 }

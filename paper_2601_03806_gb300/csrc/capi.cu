@@ -82,7 +82,11 @@ std::string flbm::validate_params(const flbm_params *p)
     if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return "tau must be finite and > 0.5";
     if (!(p->kT >= 0.0) || !std::isfinite(p->kT)) return "kT must be finite and >= 0";
     if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) return "rho0 must be finite and > 0";
-    if (p->scheme < FLBM_BGK || p->scheme > FLBM_REG) return "unknown scheme";
+    if (p->scheme < FLBM_BGK || p->scheme > FLBM_LEARNED) return "unknown scheme";
+    if (p->scheme == FLBM_LEARNED && p->precision != FLBM_FP32)
+        return "the learned collision runs on FP32 storage";
+    if (p->scheme == FLBM_LEARNED && !(p->kT > 0.0))
+        return "the learned collision needs kT > 0 (its feature scale)";
     if (p->precision < FLBM_FP64 || p->precision > FLBM_FP16) return "unknown precision";
     if (p->stats_every < 0) return "stats_every must be >= 0";
     if (p->noise_rho0 != 0 && p->noise_rho0 != 1) return "noise_rho0 must be 0 or 1";
@@ -252,6 +256,7 @@ void flbm::destroy_ctx(flbm_ctx *c)
     cudaFree(c->dstats);
     cudaFree(c->dflags);
     if (c->own_g) cudaFree(c->g);
+    cudaFree(c->mlp_img);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -321,6 +326,7 @@ int flbm::create_ctx(const flbm_params *p, void *dev_buf, size_t dev_bytes, void
         const int v = std::atoi(env);
         if (v > 0 && v < occ) per_sm = v;
     }
+    if (p->scheme == FLBM_LEARNED) per_sm = learned_occupancy(c->n);
     c->grid = int(std::min<uint64_t>(nchunks, uint64_t(c->nsm) * per_sm));
     if (c->grid < 1) c->grid = 1;
     // FLBM_INJECT_STARVE=1 (environment, failure-injection tests only): the
@@ -330,7 +336,7 @@ int flbm::create_ctx(const flbm_params *p, void *dev_buf, size_t dev_bytes, void
         if (std::atoi(inj) == 1) c->tx_pad = 16;
     // FLBM_ROWS=0 (environment) disables the TMA row pipeline
     const char *rows_env = std::getenv("FLBM_ROWS");
-    if (occ_rows > 0 && !(rows_env && std::atoi(rows_env) == 0)) {
+    if (occ_rows > 0 && p->scheme != FLBM_LEARNED && !(rows_env && std::atoi(rows_env) == 0)) {
         const uint64_t nrows = uint64_t(p->ny) * p->nz;
         c->row_grid = int(std::min<uint64_t>(nrows, uint64_t(c->nsm) * occ_rows));
     }
@@ -418,7 +424,17 @@ int flbm_step(flbm_ctx *c, int64_t n)
             }
             CK(c, cudaEventRecord(c->ev[2 * c->ev_used], c->stream));
         }
-        if (c->p.precision == FLBM_FP64)
+        if (c->p.scheme == FLBM_LEARNED) {
+            if (!c->mlp_img) return fail(c, FLBM_E_INVALID, "set the network (flbm_set_mlp) before stepping");
+            const double w[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
+            LearnArgs L;
+            L.img = c->mlp_img;
+            for (int k = 0; k < 4; ++k) L.inv_s[k] = float(1.0 / std::sqrt(c->p.rho0 * c->p.kT * w[k] * 3.0));
+            L.sig3 = float(std::pow(c->p.kT / c->p.rho0, 1.5));
+            L.x27 = float(1.0 / c->p.tau - 1.0);
+            e = launch_step_learned(static_cast<float *>(c->g), make_args<float>(c, t), L, odd, stats, c->grid,
+                                    c->stream);
+        } else if (c->p.precision == FLBM_FP64)
             e = launch_step_f64(static_cast<double *>(c->g), make_args<double>(c, t), c->p.scheme, odd,
                                 stats, c->grid, c->row_grid, c->stream);
         else if (c->p.precision == FLBM_FP32)
@@ -699,6 +715,19 @@ int flbm_set_state(flbm_ctx *c, const void *host)
     if (rc) return rc;
     CK(c, cudaStreamSynchronize(c->stream));
     return state_replaced(c);
+}
+
+int flbm_set_mlp(flbm_ctx *c, const float *params)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (!params) return fail(c, FLBM_E_INVALID, "params is NULL");
+    if (c->p.scheme != FLBM_LEARNED) return fail(c, FLBM_E_INVALID, "the context's scheme is not FLBM_LEARNED");
+    std::vector<unsigned char> img;
+    build_mlp_image(params, img);
+    if (!c->mlp_img) CK(c, cudaMalloc(&c->mlp_img, img.size()));
+    CK(c, cudaMemcpyAsync(c->mlp_img, img.data(), img.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLBM_OK;
 }
 
 int flbm_mlp_pairs(flbm_ctx *c, float *dev_x, float *dev_t)

@@ -61,6 +61,8 @@ struct flbm_ctx {
     // with it; its state may be replaced only while the ensemble's storage
     // is in the natural form
     flbm_ensemble *ens = nullptr;
+    // FLBM_LEARNED: the network image on the device (flbm_set_mlp)
+    unsigned char *mlp_img = nullptr;
     std::string err;
 };
 

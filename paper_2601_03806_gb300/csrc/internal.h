@@ -159,6 +159,17 @@ namespace flbm {
 // tensor-core operand layout (mlp_infer.cu) from the flat FP32 parameter
 // vector of include/flbm.h (FLBM_MLP_NPARAM values).
 void build_mlp_image(const float *params, std::vector<unsigned char> &img);
+// The learned step (step_learned.cu): GMF collision + network correction.
+struct LearnArgs {
+    const unsigned char *img;   // network image (build_mlp_image), device
+    float inv_s[4];             // 1 / sqrt(rho0 kT w / c_s^2) for |c|^2 = 0, 1, 2, 3
+    float sig3;                 // (kT / rho0)^(3/2)
+    float x27;                  // omega - 1
+};
+cudaError_t launch_step_learned(float *g, const StepArgs<float> &a, const LearnArgs &L, bool odd, bool stats,
+                                int grid, cudaStream_t s);
+// Resident CTAs per SM of the learned step (at most 4: tensor memory).
+int learned_occupancy(uint64_t n);
 // Training pairs (mlp_train.cu) of cn nodes from FP64 deviations g[27][cn]:
 // features X[cn][28] and targets T[cn][27] (device arrays).
 cudaError_t launch_mlp_pairs(const double *g, uint64_t cn, double rho0, double kT, double omega, float *X,

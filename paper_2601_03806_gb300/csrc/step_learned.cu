@@ -1,0 +1,156 @@
+// step_learned.cu -- the learned-collision step: GMF-FLBM (Eq. flbe2) plus
+// the network correction, fused in one kernel.
+//
+// A CTA of 128 threads takes 128 consecutive nodes of an x-row (a row chunk,
+// the chunking of the direct step kernel; threads past the row end only take
+// part in the tile).  Per chunk each thread loads its node's 27 incoming
+// populations (AA pattern), writes the node's features to the network tile,
+// and, while the first layer's tensor-core MMAs run, collides the node with
+// the GMF collision (collide_core, noise included).  Then it adds
+// P(w_i sigma^3 y_i), the network output mapped to populations with mass and
+// momentum projected out, and stores (AA pattern).  The network runs on the
+// tcgen05 path of mlp_tc.cuh.
+#include "../../include/flbm.h"
+#include "internal.h"
+#include "mlp_tc.cuh"
+
+namespace flbm {
+
+namespace {
+
+template <typename I, bool ODD, bool STATS>
+__global__ void __launch_bounds__(128, 4) k_step_learned(float *__restrict__ g, const StepArgs<float> a,
+                                                         const LearnArgs L)
+{
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    MlpSmem &sm = *reinterpret_cast<MlpSmem *>(smraw);
+    mlp_setup(sm, L.img);
+    uint32_t phase = 0;
+    float acc[NSTAT];
+#pragma unroll
+    for (int s = 0; s < NSTAT; ++s) acc[s] = 0.0f;
+    const I N = I(a.n);
+    for (uint64_t ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x) {
+        const uint32_t xc = uint32_t(ch % a.cpr);
+        const uint64_t r = ch / a.cpr;
+        const uint32_t y = uint32_t(r % a.ny);
+        const uint32_t z = uint32_t(r / a.ny);
+        const uint32_t x = xc * 128 + threadIdx.x;
+        const bool active = x < a.nx;
+        const Nbr<I> nb(active ? x : 0, y, z, a.nx, a.ny, a.nz);
+        const I n = nb.node();
+        float v[3][3][3];
+        float xf[kMlpIn];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    I idx;
+                    if (!ODD) idx = I(slot_of(i - 1, j - 1, k - 1)) * N + n;
+                    else idx = I(slot_of(1 - i, 1 - j, 1 - k)) * N + (nb.xs[2 - i] + nb.ry[2 - j] + nb.rz[2 - k]);
+                    v[i][j][k] = active ? __ldcg(g + idx) : 0.0f;
+                    // feature of population c = (i-1, j-1, k-1): g_c / sqrt(rho0 kT w_c / c_s^2)
+                    xf[slot_of(i - 1, j - 1, k - 1)] = v[i][j][k] * L.inv_s[(i != 1) + (j != 1) + (k != 1)];
+                }
+        xf[27] = active ? L.x27 : 0.0f;
+        float yv[kMlpOut];
+        float nzd[kNoise];   // unused: the collision draws its normals inside
+        const bool ok = mlp_tile(sm, phase, xf, yv, [&] {
+            if (active) collide_core<float, 1, STATS, false>(v, a, nzd, uint32_t(n), acc);
+        });
+        if (!ok) {
+            if (threadIdx.x == 0) atomicOr(a.flag, 2u);
+            break;
+        }
+        if (!active) continue;
+        // correction d_c = w_c sigma^3 y_c, minus its mass and momentum
+        float d[3][3][3];
+        float alpha = 0.0f, bx = 0.0f, by = 0.0f, bz = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float w = float(w1(i - 1) * w1(j - 1) * w1(k - 1));
+                    const float dv = w * L.sig3 * yv[slot_of(i - 1, j - 1, k - 1)];
+                    d[i][j][k] = dv;
+                    alpha += dv;
+                    bx += dv * float(i - 1);
+                    by += dv * float(j - 1);
+                    bz += dv * float(k - 1);
+                }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float w = float(w1(i - 1) * w1(j - 1) * w1(k - 1));
+                    const float cb = bx * float(i - 1) + by * float(j - 1) + bz * float(k - 1);
+                    v[i][j][k] += d[i][j][k] - w * (alpha + 3.0f * cb);
+                }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    I idx;
+                    if (!ODD) idx = I(slot_of(1 - i, 1 - j, 1 - k)) * N + n;
+                    else idx = I(slot_of(i - 1, j - 1, k - 1)) * N + (nb.xs[i] + nb.ry[j] + nb.rz[k]);
+                    __stcs(g + idx, v[i][j][k]);
+                }
+    }
+    mlp_teardown(sm);
+    if (STATS) block_reduce_store(acc, a.partials + size_t(blockIdx.x) * NSTAT);
+}
+
+template <typename I>
+cudaError_t launch_t(float *g, const StepArgs<float> &a, const LearnArgs &L, bool odd, bool stats, int grid,
+                     cudaStream_t s)
+{
+    if (odd) {
+        if (stats) k_step_learned<I, true, true><<<grid, 128, kMlpSmemBytes, s>>>(g, a, L);
+        else k_step_learned<I, true, false><<<grid, 128, kMlpSmemBytes, s>>>(g, a, L);
+    } else {
+        if (stats) k_step_learned<I, false, true><<<grid, 128, kMlpSmemBytes, s>>>(g, a, L);
+        else k_step_learned<I, false, false><<<grid, 128, kMlpSmemBytes, s>>>(g, a, L);
+    }
+    return cudaGetLastError();
+}
+
+bool fits32(uint64_t n) { return n * kQ < (1ull << 32); }
+
+}  // namespace
+
+cudaError_t launch_step_learned(float *g, const StepArgs<float> &a, const LearnArgs &L, bool odd, bool stats,
+                                int grid, cudaStream_t s)
+{
+    if (fits32(a.n)) return launch_t<uint32_t>(g, a, L, odd, stats, grid, s);
+    return launch_t<uint64_t>(g, a, L, odd, stats, grid, s);
+}
+
+int learned_occupancy(uint64_t n)
+{
+    // static (reduction) + dynamic shared memory exceed the 48 KB default
+    const int sm = int(kMlpSmemBytes);
+    cudaFuncSetAttribute(k_step_learned<uint32_t, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_step_learned<uint32_t, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_step_learned<uint32_t, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_step_learned<uint32_t, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_step_learned<uint64_t, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_step_learned<uint64_t, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_step_learned<uint64_t, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_step_learned<uint64_t, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    int nb = 0;
+    const cudaError_t e = fits32(n)
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_learned<uint32_t, true, true>, 128, kMlpSmemBytes)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_learned<uint64_t, true, true>, 128, kMlpSmemBytes);
+    if (e != cudaSuccess || nb < 1) return 1;
+    return nb < 4 ? nb : 4;   // 128 tensor-memory columns per CTA, 512 per SM
+}
+
+}  // namespace flbm

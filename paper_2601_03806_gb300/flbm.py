@@ -17,13 +17,13 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libflbm.so")
 
-FLBM_BGK, FLBM_GMF, FLBM_REG = 0, 1, 2
+FLBM_BGK, FLBM_GMF, FLBM_REG, FLBM_LEARNED = 0, 1, 2, 3
 FLBM_FP64, FLBM_FP32, FLBM_FP16 = 0, 1, 2
 FLBM_OK, FLBM_E_INVALID, FLBM_E_NOMEM, FLBM_E_CUDA = 0, -1, -2, -3
 FLBM_E_UNSTABLE, FLBM_E_TIMEOUT, FLBM_E_UNSUPPORTED = -4, -5, -6
 (FLBM_OBS_RHO, FLBM_OBS_JSUM, FLBM_OBS_PI_DIAG, FLBM_OBS_PI_OFFDIAG,
  FLBM_OBS_JX, FLBM_OBS_JY, FLBM_OBS_JZ) = range(7)
-SCHEMES = {"bgk": FLBM_BGK, "gmf": FLBM_GMF, "reg": FLBM_REG}
+SCHEMES = {"bgk": FLBM_BGK, "gmf": FLBM_GMF, "reg": FLBM_REG, "learned": FLBM_LEARNED}
 PRECISIONS = {"fp64": FLBM_FP64, "fp32": FLBM_FP32, "fp16": FLBM_FP16}
 Q = 27
 
@@ -105,6 +105,7 @@ def _load():
         "flbm_ensemble_destroy": ([vp], None),
         "flbm_mlp_infer": ([vp, vp, i64, vp], i32),
         "flbm_mlp_pairs": ([vp, vp, vp], i32),
+        "flbm_set_mlp": ([vp, vp], i32),
         "flbm_mlp_grad": ([vp, vp, vp, i64, vp, vp], i32),
         "flbm_mlp_train": ([vp, vp, vp, i64, i32, i32, d, u64, vp], i32),
     }
@@ -154,6 +155,7 @@ flbm_ensemble_last_error = lib.flbm_ensemble_last_error
 flbm_ensemble_destroy = lib.flbm_ensemble_destroy
 flbm_mlp_infer = lib.flbm_mlp_infer
 flbm_mlp_pairs = lib.flbm_mlp_pairs
+flbm_set_mlp = lib.flbm_set_mlp
 flbm_mlp_grad = lib.flbm_mlp_grad
 flbm_mlp_train = lib.flbm_mlp_train
 MLP_NPARAM = 7771
@@ -264,6 +266,13 @@ class _CtxOps:
 
     def stats_reset(self) -> None:
         self._check(lib.flbm_stats_reset(self._h))
+
+    def set_mlp(self, params) -> None:
+        """Network of a learned-scheme context (7771 float parameters)."""
+        p = np.ascontiguousarray(params, np.float32)
+        if p.size != MLP_NPARAM:
+            raise ValueError("params must hold %d values" % MLP_NPARAM)
+        self._check(lib.flbm_set_mlp(self._h, _ptr(p)))
 
     def mlp_pairs(self, dev_x, dev_t) -> None:
         """Training pairs of every node into CUDA tensors x[N, 28], t[N, 27]."""

@@ -157,3 +157,102 @@ def test_training_learns_the_regularized_correction(F, M, torch_cuda):
     rel = np.linalg.norm(y - t) / np.linalg.norm(t)
     print("held-out relative error of the learned correction: %.4f (GMF: 1)" % rel)
     assert rel < 0.06
+
+
+# ---------------------------------------------------------------------------
+# The learned step (scheme FLBM_LEARNED): GMF collision + network correction
+
+
+def streamed(O, field):
+    """f_i(x) <- field_i(x - c_i) on the periodic box, field[27, nz, ny, nx]."""
+    c = O.tables()["c"]
+    out = np.empty_like(field)
+    for i in range(27):
+        out[i] = np.roll(field[i], shift=(c[i, 2], c[i, 1], c[i, 0]), axis=(0, 1, 2))
+    return out
+
+
+@pytest.mark.parametrize("shape", [(130, 4, 3), (64, 2, 1), (32, 3, 2)])
+def test_learned_step_correction_matches_oracle(F, M, oracle_mod, shape):
+    """One learned step minus one GMF step from the same state with the same
+    noise leaves the network correction P(w sigma^3 y), streamed; it must
+    match the oracle's within the propagated bf16/tanh bound of y (plus the
+    FP32 rounding of two stored states, 1e-8).  kT = 1e-3 puts the
+    correction well above that rounding."""
+    O = oracle_mod
+    nx, ny, nz = shape
+    tau, kT, rho0 = 0.8, 1e-3, 1.0
+    theta = random_net(M, 21)
+    boxes = {}
+    for scheme in (F.FLBM_GMF, F.FLBM_LEARNED):
+        b = F.Lattice(nx, ny, nz, tau, kT, rho0=rho0, seed=8, scheme=scheme)
+        b.init_thermal(3)
+        boxes[scheme] = b
+    boxes[F.FLBM_LEARNED].set_mlp(theta)
+    f0 = boxes[F.FLBM_LEARNED].get_populations()
+    for b in boxes.values():
+        b.step(1)
+    D = boxes[F.FLBM_LEARNED].get_populations() - boxes[F.FLBM_GMF].get_populations()
+    fn = f0.reshape(27, -1).T
+    corr = M.correction(theta, fn, rho0, kT, 1.0 / tau, bf16=True)
+    # bound on the correction error from the bound on y
+    w = O.tables()["w"]
+    c = O.tables()["c"]
+    _, ey = bound(M, theta, M.features(fn, rho0, kT, 1.0 / tau))
+    dlt = w * (kT / rho0) ** 1.5 * ey
+    eb = dlt + w * (1 + 3 * np.abs(c).sum(1)) * dlt.sum(1, keepdims=True) + 1e-8
+    expect = streamed(O, corr.T.reshape(27, nz, ny, nx))
+    ebound = streamed(O, eb.T.reshape(27, nz, ny, nx))
+    err = np.abs(D - expect)
+    assert np.all(err <= ebound), (err.max(), (err / ebound).max())
+    assert np.abs(expect).max() > 100 * 1e-8
+
+
+def test_learned_step_conserves_and_needs_its_network(F, M):
+    nx, ny, nz, tau, kT = 64, 4, 4, 0.7, 1e-4
+    b = F.Lattice(nx, ny, nz, tau, kT, seed=2, scheme=F.FLBM_LEARNED)
+    b.init_thermal(1)
+    with pytest.raises(F.FlbmError) as ei:
+        b.step(1)
+    assert ei.value.code == F.FLBM_E_INVALID
+    b.set_mlp(random_net(M, 4))
+    rho, j, _ = b.moments()
+    b.step(6)
+    rho2, j2, _ = b.moments()
+    assert abs(rho2.sum() - rho.sum()) < 1e-6 * rho.size * 1e-3
+    assert np.abs(j2.sum(axis=(1, 2, 3)) - j.sum(axis=(1, 2, 3))).max() < 1e-6
+    for kw in (dict(precision=F.FLBM_FP16), dict(precision=F.FLBM_FP64)):
+        with pytest.raises(F.FlbmError):
+            F.Lattice(nx, ny, nz, tau, kT, scheme=F.FLBM_LEARNED, **kw)
+    with pytest.raises(F.FlbmError):
+        F.Lattice(nx, ny, nz, tau, 0.0, scheme=F.FLBM_LEARNED)
+    g = F.Lattice(nx, ny, nz, tau, kT, scheme=F.FLBM_GMF)
+    with pytest.raises(F.FlbmError):
+        g.set_mlp(random_net(M, 4))
+
+
+def test_learned_equipartition_and_flat_spectrum(F, M, torch_cuda):
+    """Config-5 statistics on a 64^3 box (tau 0.8, kT 1e-5) with a network
+    trained on Reg-FLBM pairs: <u_a^2> = kT/rho0 and S_jx(k) = rho0 kT,
+    within the sampling noise, as for plain GMF-FLBM."""
+    torch = torch_cuda
+    X, T = reg_pairs(F, torch, [0.51, 0.9, 1.7, 3.0])
+    theta, _ = F.mlp_train(M.init_params(2).astype(np.float32), X, T, epochs=60, batch=1024, lr=1e-2, seed=7)
+    out = {}
+    for scheme in (F.FLBM_GMF, F.FLBM_LEARNED):
+        b = F.Lattice(64, 64, 64, 0.8, 1e-5, seed=12, scheme=scheme)
+        if scheme == F.FLBM_LEARNED:
+            b.set_mlp(theta)
+        b.init_thermal(6)
+        b.step(20)
+        b.stats_reset()
+        b.step(200)
+        S, cnt = b.structure_factor(F.FLBM_OBS_JX, 32)
+        m = cnt > 0
+        out[scheme] = (np.array(b.stats()["u2_avg"]) / 1e-5,
+                       np.sum(S[m] * cnt[m]) / np.sum(cnt[m]) / 1e-5)
+    for scheme, (u2, s) in out.items():
+        print(scheme, u2, s)
+        assert np.all(np.abs(u2 - 1) < 0.02), (scheme, u2)
+        assert abs(s - 1) < 0.03, (scheme, s)
+    assert np.all(np.abs(out[F.FLBM_LEARNED][0] - out[F.FLBM_GMF][0]) < 0.01)
