@@ -55,11 +55,14 @@ def parse_args(argv=None):
                     help="population storage (fp32 = the benchmark workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", choices=["box", "ensemble"], default="box",
+    ap.add_argument("--workload", choices=["box", "ensemble", "learned"], default="box",
                     help="box: one 512^3 box (default); ensemble: 256 x 32^3 + 64 x 64^3 + "
                          "8 x 128^3 replicas in one persistent kernel per step")
     ap.add_argument("--no-plain", action="store_true",
                     help="ensemble: skip timing the same replicas one box at a time")
+    ap.add_argument("--train-boxes", type=int, default=64,
+                    help="learned: Reg-FLBM 64^3 boxes whose pairs train the network (64 = 2^24 pairs)")
+    ap.add_argument("--train-epochs", type=int, default=6)
     ap.add_argument("--ens-div", type=int, default=1,
                     help="ensemble: divide every replica count by this (profiling runs; 1 = the "
                          "benchmark workload)")
@@ -609,6 +612,186 @@ def run_ensemble(args, rank, local, ws):
     return 0
 
 
+# ----------------------------------------------------------------------------
+# learned collision
+
+
+def run_learned(args, rank, local, ws):
+    """Config 5: a network trained on Reg-FLBM pre/post-collision pairs
+    (64^3 boxes, tau ~ U[0.51, 3.0], kT = 1e-5) corrects GMF-FLBM on a 256^3
+    box (tau 0.8, kT 1e-5); timed like the box workload and compared with
+    plain GMF-FLBM on the same GPU."""
+    import numpy as np
+    import torch
+    from paper_2601_03806_gb300 import build as _b
+    _b.build()
+    from paper_2601_03806_gb300 import flbm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seed = WORKLOAD["seed"] + rank
+    kT, rho0, tau = WORKLOAD["kT"], WORKLOAD["rho0"], 0.8
+    n = args.size if args.size != 512 else 256
+    N = n ** 3
+    rng = np.random.default_rng(seed)
+
+    def pairs(taus, start):
+        xs, ts = [], []
+        for r, tb in enumerate(taus):
+            box = flbm.Lattice(64, 64, 64, float(tb), kT, seed=seed, scheme=flbm.FLBM_REG,
+                               noise_stream=start + r)
+            box.init_thermal(seed * 7 + start + r)
+            box.step(40)
+            X = torch.empty((64 ** 3, 28), dtype=torch.float32, device=dev)
+            T = torch.empty((64 ** 3, 27), dtype=torch.float32, device=dev)
+            box.mlp_pairs(X, T)
+            xs.append(X)
+            ts.append(T)
+            box.close()
+        return torch.cat(xs), torch.cat(ts)
+
+    t0 = time.perf_counter()
+    X, T = pairs(rng.uniform(0.51, 3.0, size=args.train_boxes), 0)
+    t1 = time.perf_counter()
+    # initial parameters: He-style normal weights, zero biases (seeded)
+    nin, nh, nout = 28, 64, 27
+    theta0 = np.concatenate([rng.normal(0, np.sqrt(1.0 / nin), nh * nin), np.zeros(nh),
+                             rng.normal(0, np.sqrt(1.0 / nh), nh * nh), np.zeros(nh),
+                             rng.normal(0, np.sqrt(1.0 / nh), nout * nh), np.zeros(nout)]).astype(np.float32)
+    theta, losses = flbm.mlp_train(theta0, X, T, epochs=args.train_epochs, batch=1024, lr=1e-2, seed=seed)
+    t2 = time.perf_counter()
+    del X, T
+    Xh, Th = pairs([tau], 10 ** 6)
+    yh = flbm.mlp_infer(theta, Xh.cpu().numpy())
+    th = Th.cpu().numpy()
+    rel = float(np.linalg.norm(yh - th) / np.linalg.norm(th))
+    del Xh, Th
+    training = {"pairs": args.train_boxes * 64 ** 3, "epochs": args.train_epochs, "batch": 1024,
+                "first_epoch_loss": float(losses[0]), "last_epoch_loss": float(losses[-1]),
+                "pairs_s": t1 - t0, "train_s": t2 - t1,
+                "held_out_rel_error_of_correction": rel, "gmf_rel_error": 1.0}
+
+    stream = torch.cuda.Stream(device=dev)
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    gpu_id = ("GPU-" + str(uuid)) if uuid is not None else os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]
+
+    def timed(scheme):
+        lat = flbm.Lattice(n, n, n, tau, kT, rho0=rho0, seed=seed, scheme=scheme, stats_every=1,
+                           torch_memory=True, stream=stream)
+        if scheme == flbm.FLBM_LEARNED:
+            lat.set_mlp(theta)
+        lat.init_thermal(seed)
+        lat.step(args.warmup)
+        lat.stats_reset()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier(ws)
+        with ClockSampler(gpu_id) as clk:
+            lat.timing_enable(True)
+            start.record(stream)
+            lat.step(args.steps)
+            end.record(stream)
+            torch.cuda.synchronize()
+        kms, launches = lat.timing_read()
+        lat.timing_enable(False)
+        barrier(ws)
+        el = start.elapsed_time(end)
+        st = lat.stats()
+        return lat, el, kms / max(launches, 1), launches, clk.summary(), st
+
+    lat, el_ms, k_ms, launches, clocks, st = timed(flbm.FLBM_LEARNED)
+    max_ms = max_over_ranks(el_ms, ws, dev)
+    value = job_mlups(N, args.steps, max_ms, ws)
+    peak, peak_src = measured_hbm_peak()
+    achieved = BYTES_PER_NODE["fp32"] * N / (k_ms / 1e3) / 1e9
+    flop_node = 2 * 128 * (32 * 64 + 64 * 64 + 64 * 32) // 128   # padded MMA shapes per node
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            tpk, tsrc = float(json.load(fh)["bf16_tflops_sustained"]), "of measured (sustained)"
+    except Exception:
+        tpk, tsrc = 1700.0, "of fallback"
+    tflops = flop_node * N / (k_ms / 1e3) / 1e12
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_src, "traffic": None,
+                "kernel": "flbm::k_step_learned<uint32,*,stats> (GMF + tcgen05 MLP correction)",
+                "kernel_ms": k_ms, "algorithmic_bytes_per_launch": BYTES_PER_NODE["fp32"] * N,
+                "tensor": {"achieved_tflops": tflops, "peak_tflops": tpk, "frac": tflops / tpk,
+                           "peak_source": tsrc, "flop_per_node": flop_node}}
+    u2 = [x / (kT / rho0) for x in st["u2_avg"]]
+
+    e2e = None
+    if not args.no_e2e:
+        hstate = torch.empty(27 * N, dtype=torch.float32, pin_memory=True)
+        lat.get_state(hstate)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.set_state(hstate)
+        for _ in range(args.steps):
+            lat.step(1)
+            lat.stats()
+        torch.cuda.synchronize()
+        e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, ws, dev)
+        import ctypes
+        e2e = {"value": job_mlups(N, args.steps, e_ms, ws), "unit": "MLUPS",
+               "h2d_bytes_per_step": 4 * 27 * N // args.steps,
+               "d2h_bytes_per_step": ctypes.sizeof(flbm.flbm_stats_t) + 16,
+               "what": "flbm_set_state from pinned host + K x (flbm_step(1) + flbm_stats)"}
+        del hstate
+    lat.close()
+    glat, gel, gk_ms, _, _, gst = timed(flbm.FLBM_GMF)
+    glat.close()
+    plain = {"value": job_mlups(N, args.steps, max_over_ranks(gel, ws, dev), ws), "unit": "MLUPS",
+             "what": "plain GMF-FLBM (row pipeline) on the same box",
+             "u2_avg_over_kT_rho0": [x / (kT / rho0) for x in gst["u2_avg"]]}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+        from oracle import mlp as omlp
+        oracle.build()
+        threads = os.cpu_count() or 1
+        oracle.set_threads(threads)
+        m = 32
+        w = oracle.tables()["w"]
+        box = oracle.Box(m, m, m, tau, kT, rho0=rho0, seed=seed)
+        steps, t0 = 0, time.perf_counter()
+        while True:
+            # the oracle's work per learned step: the network correction of
+            # every node (numpy, FP64) and the GMF collision with streaming
+            omlp.correction(theta, box.get_f().reshape(27, -1).T, rho0, kT, 1.0 / tau)
+            box.step(1)
+            steps += 1
+            if time.perf_counter() - t0 > 2.0 and steps >= 3:
+                break
+        el = time.perf_counter() - t0
+        cpu = {"value": m ** 3 * steps / el / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+               "sample": "32^3 box, %d steps, each the oracle's network correction of every node "
+                         "(numpy FP64) and its GMF collision + streaming (C, %d threads)" % (steps, threads)}
+    if rank == 0:
+        line = {
+            "metric": "MLUPS of the learned-collision step (GMF-FLBM + tcgen05 network correction)",
+            "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (network: bf16 operands, f32 accumulation)",
+            "data": "synthetic",
+            "config": {"workload": "learned collision: %d^3 box, tau 0.8, kT 1e-5, FP32 deviations AA in "
+                                   "place, network 28-64-64-27 trained on %d Reg-FLBM pairs from 64^3 boxes "
+                                   "with tau ~ U[0.51, 3.0]" % (n, args.train_boxes * 64 ** 3),
+                       "nx": n, "ny": n, "nz": n, "tau": tau, "kT": kT, "rho0": rho0,
+                       "l2": "inputs larger than L2 (%.2f GB state vs 129 MB L2)" % (108 * N / 1e9),
+                       "parallelism": "replicas x%d" % ws},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain_kernel": plain,
+            "gpu_launches": int(launches) + int(args.steps), "clocks": clocks,
+            "training": training,
+            "equipartition": {"u2_avg_over_kT_rho0": u2, "max_abs_error": max(abs(x - 1) for x in u2),
+                              "samples": st["n_samples"]},
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     rank, local, ws = dist_setup()
@@ -617,6 +800,8 @@ def main(argv=None):
             return run_reference(args, rank, ws)
         if args.workload == "ensemble":
             return run_ensemble(args, rank, local, ws)
+        if args.workload == "learned":
+            return run_learned(args, rank, local, ws)
         return run_ours(args, rank, local, ws)
     finally:
         if ws > 1:

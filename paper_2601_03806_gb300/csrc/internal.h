@@ -168,7 +168,8 @@ struct LearnArgs {
 };
 cudaError_t launch_step_learned(float *g, const StepArgs<float> &a, const LearnArgs &L, bool odd, bool stats,
                                 int grid, cudaStream_t s);
-// Resident CTAs per SM of the learned step (at most 4: tensor memory).
+// Resident CTAs per SM of the learned step (1: a CTA holds all of an SM's
+// tensor memory); also sets the kernels' shared-memory attribute.
 int learned_occupancy(uint64_t n);
 // Training pairs (mlp_train.cu) of cn nodes from FP64 deviations g[27][cn]:
 // features X[cn][28] and targets T[cn][27] (device arrays).

@@ -26,7 +26,7 @@ uint16_t bf16_rne(float f)
 
 void put(std::vector<unsigned char> &img, uint32_t off, uint16_t v) { std::memcpy(&img[off], &v, 2); }
 
-__global__ void __launch_bounds__(128) k_mlp_infer(const float *__restrict__ x, float *__restrict__ y,
+__global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_infer(const float *__restrict__ x, float *__restrict__ y,
                                                    uint64_t n, const unsigned char *__restrict__ img,
                                                    unsigned int *flag)
 {
@@ -34,9 +34,9 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const float *__restrict__ x, 
     MlpSmem &sm = *reinterpret_cast<MlpSmem *>(smraw);
     mlp_setup(sm, img);
     uint32_t phase = 0;
-    const uint64_t ntiles = (n + 127) / 128;
+    const uint64_t ntiles = (n + kMlpThreads - 1) / kMlpThreads;
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint64_t row = tile * 128 + threadIdx.x;
+        const uint64_t row = tile * kMlpThreads + threadIdx.x;
         float xr[kMlpIn];
 #pragma unroll
         for (int i = 0; i < kMlpIn; ++i) xr[i] = row < n ? x[row * kMlpIn + i] : 0.0f;
@@ -117,9 +117,12 @@ extern "C" int flbm_mlp_infer(const float *params, const float *x, int64_t n, fl
     if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x, size_t(n) * kMlpIn * sizeof(float), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dflag, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return done(FLBM_E_CUDA, "upload", e);
-    const uint64_t ntiles = (uint64_t(n) + 127) / 128;
-    const int grid = int(std::min<uint64_t>(ntiles, uint64_t(nsm) * 4));
-    k_mlp_infer<<<grid, 128, kMlpSmemBytes, s>>>(dx, dy, uint64_t(n), dimg, dflag);
+    // one CTA per SM (a kernel that allocates tensor memory gets no more)
+    const uint64_t ntiles = (uint64_t(n) + kMlpThreads - 1) / kMlpThreads;
+    const int grid = int(std::min<uint64_t>(ntiles, uint64_t(nsm)));
+    e = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMlpSmemBytes));
+    if (e != cudaSuccess) return done(FLBM_E_CUDA, "shared-memory attribute", e);
+    k_mlp_infer<<<grid, kMlpThreads, kMlpSmemBytes, s>>>(dx, dy, uint64_t(n), dimg, dflag);
     e = cudaGetLastError();
     if (e != cudaSuccess) return done(FLBM_E_CUDA, "launch", e);
     e = cudaMemcpyAsync(y, dy, size_t(n) * kMlpOut * sizeof(float), cudaMemcpyDeviceToHost, s);

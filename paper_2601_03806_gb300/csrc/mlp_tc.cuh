@@ -2,7 +2,11 @@
 // weights, FP32 accumulation) on the tcgen05 tensor cores, one tile of 128
 // nodes per CTA at a time.
 //
-// A CTA of 128 threads: thread t owns tile row t (one node).  Per tile
+// A kernel that allocates tensor memory gets one CTA per SM, so a CTA runs
+// four independent sub-tiles of 128 rows at once: 512 threads, thread t owns
+// row t % 128 of sub-tile t / 128 (warp w reads tensor-memory lanes
+// 32 (w % 4) .. + 31, its rows), and sub-tile q owns tensor-memory columns
+// 128 q .. 128 q + 127 (all 512 columns of the SM).  Per sub-tile
 //   A1[128 x 32]  bf16 features (28 + 4 zero columns)      -> shared memory
 //   D1 = A1 W1^T  (M 128, N 64, K 32: two MMAs)             -> tensor memory cols 0..63
 //   h1 = silu(D1 + b1) as bf16                               -> A2 (shared)
@@ -10,12 +14,10 @@
 //   h2 = silu(D2 + b2) as bf16                               -> A2 again
 //   D3 = h2 W3^T  (N 32, K 64: four MMAs; rows 27..31 of W3 are zero) -> cols 0..31
 //   y = D3 + b3                                              -> thread t's registers
-// One elected thread issues the MMAs; their completion arrives on an
-// mbarrier that every thread waits on (bounded).  The weight image (bf16,
-// already in the operand layout of umma.cuh) and the FP32 biases are copied
-// into shared memory once per CTA.  128 tensor-memory columns per CTA; the
-// shared-memory footprint keeps at most 4 CTAs on an SM, so the 512 columns
-// of an SM are never over-subscribed.
+// One elected thread issues the MMAs of all four sub-tiles; their completion
+// arrives on one mbarrier that every thread waits on (bounded).  The weight
+// image (bf16, already in the operand layout of umma.cuh) and the FP32
+// biases are copied into shared memory once per CTA.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -30,18 +32,19 @@ constexpr uint32_t kSbo32 = 4 * 128;          // SBO of a K = 32 operand
 constexpr uint32_t kSbo64 = 8 * 128;          // SBO of a K = 64 operand
 constexpr uint32_t kW1Off = 0, kW2Off = 4096, kW3Off = 12288, kBiasOff = 16384;
 constexpr uint32_t kMlpImageBytes = kBiasOff + (64 + 64 + 32) * 4;   // 17,024 B
-constexpr uint32_t kMlpTmemCols = 128;
-constexpr size_t kMlpSmemBytes = 47 * 1024;   // >= sizeof(MlpSmem); <= 4 CTAs per SM
+constexpr uint32_t kMlpSub = 4;                 // sub-tiles of 128 rows per CTA
+constexpr uint32_t kMlpThreads = 128 * kMlpSub;  // CTA size
+constexpr uint32_t kMlpTmemCols = 128 * kMlpSub; // the whole tensor memory of an SM
 
 struct MlpSmem {
     __align__(128) unsigned char w[kBiasOff];          // W1 | W2 | W3 bf16 images
     float bias[64 + 64 + 32];                          // b1 | b2 | b3 (b3 zero-padded)
-    __align__(128) unsigned char a1[128 * 32 * 2];
-    __align__(128) unsigned char a2[128 * 64 * 2];
+    __align__(128) unsigned char a1[kMlpSub][128 * 32 * 2];
+    __align__(128) unsigned char a2[kMlpSub][128 * 64 * 2];
     uint64_t bar;
     uint32_t tmem;
 };
-static_assert(sizeof(MlpSmem) <= kMlpSmemBytes, "MlpSmem exceeds its shared-memory budget");
+constexpr size_t kMlpSmemBytes = (sizeof(MlpSmem) + 1023) / 1024 * 1024;
 
 // silu(z) = z sigmoid(z) = 0.5 z (1 + tanh(z / 2)), with the hardware tanh
 // (absolute error about 2^-11, below the bf16 rounding of the activations).
@@ -119,35 +122,39 @@ __device__ __forceinline__ void mlp_sync_for_mma()
     __syncthreads();
 }
 
-// One tile: x = this thread's 28 features (row threadIdx.x), y = its 27
-// outputs.  work() runs while the first layer's MMAs are in flight.  Returns
+// One round: x = this thread's 28 features (row t % 128 of sub-tile t / 128),
+// y = its 27 outputs.  work() runs while the first layer's MMAs are in flight.  Returns
 // false (on every thread) if a wait ran out; the MMAs are then drained with
 // one more bounded wait before returning.
 template <typename Work>
 __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const float (&x)[kMlpIn],
                                          float (&y)[kMlpOut], Work &&work)
 {
-    const uint32_t t = threadIdx.x;
-    const uint32_t tmem = sm.tmem;
-    const uint32_t lane_base = (t & ~31u) << 16;
-    const uint32_t w = smem_u32(sm.w), a1 = smem_u32(sm.a1), a2 = smem_u32(sm.a2);
+    const uint32_t t = threadIdx.x & 127u, q = threadIdx.x >> 7;
+    const uint32_t tmem = sm.tmem + 128u * q;                 // this sub-tile's columns
+    const uint32_t lane_base = ((threadIdx.x >> 5) & 3u) << 21;   // (32 (warp % 4)) << 16
+    const uint32_t w = smem_u32(sm.w);
+    unsigned char *a1p = sm.a1[q], *a2p = sm.a2[q];
     constexpr uint32_t idesc64 = umma_idesc_bf16(128, 64), idesc32 = umma_idesc_bf16(128, 32);
     {
         float v[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = x[i];
-        store_row16(sm.a1, kSbo32, t, 0, v);
+        store_row16(a1p, kSbo32, t, 0, v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = (16 + i < kMlpIn) ? x[16 + i] : 0.0f;
-        store_row16(sm.a1, kSbo32, t, 16, v);
+        store_row16(a1p, kSbo32, t, 16, v);
     }
     mlp_sync_for_mma();
-    if (t == 0) {
+    if (threadIdx.x == 0) {
         tc_fence_after();
+        for (uint32_t qq = 0; qq < kMlpSub; ++qq) {
+            const uint32_t a1 = smem_u32(sm.a1[qq]);
 #pragma unroll
-        for (uint32_t s = 0; s < 2; ++s)
-            umma_bf16(tmem, umma_smem_desc(a1 + 256 * s, 128, kSbo32),
-                      umma_smem_desc(w + kW1Off + 256 * s, 128, kSbo32), idesc64, s > 0);
+            for (uint32_t s = 0; s < 2; ++s)
+                umma_bf16(sm.tmem + 128u * qq, umma_smem_desc(a1 + 256 * s, 128, kSbo32),
+                          umma_smem_desc(w + kW1Off + 256 * s, 128, kSbo32), idesc64, s > 0);
+        }
         umma_commit(&sm.bar);
     }
     work();
@@ -159,15 +166,18 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
             tmem_ld16(tmem + lane_base + 16 * ch, z);
 #pragma unroll
             for (int i = 0; i < 16; ++i) z[i] = silu_fast(z[i] + sm.bias[16 * ch + i]);
-            store_row16(sm.a2, kSbo64, t, 16 * ch, z);
+            store_row16(a2p, kSbo64, t, 16 * ch, z);
         }
         mlp_sync_for_mma();
-        if (t == 0) {
+        if (threadIdx.x == 0) {
             tc_fence_after();
+            for (uint32_t qq = 0; qq < kMlpSub; ++qq) {
+                const uint32_t a2 = smem_u32(sm.a2[qq]);
 #pragma unroll
-            for (uint32_t s = 0; s < 4; ++s)
-                umma_bf16(tmem + 64, umma_smem_desc(a2 + 256 * s, 128, kSbo64),
-                          umma_smem_desc(w + kW2Off + 256 * s, 128, kSbo64), idesc64, s > 0);
+                for (uint32_t s = 0; s < 4; ++s)
+                    umma_bf16(sm.tmem + 128u * qq + 64, umma_smem_desc(a2 + 256 * s, 128, kSbo64),
+                              umma_smem_desc(w + kW2Off + 256 * s, 128, kSbo64), idesc64, s > 0);
+            }
             umma_commit(&sm.bar);
         }
         ok = mlp_wait(sm, phase);
@@ -179,15 +189,18 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
             tmem_ld16(tmem + lane_base + 64 + 16 * ch, z);
 #pragma unroll
             for (int i = 0; i < 16; ++i) z[i] = silu_fast(z[i] + sm.bias[64 + 16 * ch + i]);
-            store_row16(sm.a2, kSbo64, t, 16 * ch, z);
+            store_row16(a2p, kSbo64, t, 16 * ch, z);
         }
         mlp_sync_for_mma();
-        if (t == 0) {
+        if (threadIdx.x == 0) {
             tc_fence_after();
+            for (uint32_t qq = 0; qq < kMlpSub; ++qq) {
+                const uint32_t a2 = smem_u32(sm.a2[qq]);
 #pragma unroll
-            for (uint32_t s = 0; s < 4; ++s)
-                umma_bf16(tmem, umma_smem_desc(a2 + 256 * s, 128, kSbo64),
-                          umma_smem_desc(w + kW3Off + 256 * s, 128, kSbo64), idesc32, s > 0);
+                for (uint32_t s = 0; s < 4; ++s)
+                    umma_bf16(sm.tmem + 128u * qq, umma_smem_desc(a2 + 256 * s, 128, kSbo64),
+                              umma_smem_desc(w + kW3Off + 256 * s, 128, kSbo64), idesc32, s > 0);
+            }
             umma_commit(&sm.bar);
         }
         ok = mlp_wait(sm, phase);

@@ -1,9 +1,11 @@
 // step_learned.cu -- the learned-collision step: GMF-FLBM (Eq. flbe2) plus
 // the network correction, fused in one kernel.
 //
-// A CTA of 128 threads takes 128 consecutive nodes of an x-row (a row chunk,
-// the chunking of the direct step kernel; threads past the row end only take
-// part in the tile).  Per chunk each thread loads its node's 27 incoming
+// A CTA of 512 threads (one per SM: it allocates tensor memory) takes four
+// row chunks of 128 consecutive x-nodes (the chunking of the direct step
+// kernel) at a time, one per network sub-tile; threads past a row end or
+// past the last chunk only take part in the tile.  Each thread loads its
+// node's 27 incoming
 // populations (AA pattern), writes the node's features to the network tile,
 // and, while the first layer's tensor-core MMAs run, collides the node with
 // the GMF collision (collide_core, noise included).  Then it adds
@@ -19,7 +21,7 @@ namespace flbm {
 namespace {
 
 template <typename I, bool ODD, bool STATS>
-__global__ void __launch_bounds__(128, 4) k_step_learned(float *__restrict__ g, const StepArgs<float> a,
+__global__ void __launch_bounds__(kMlpThreads, 1) k_step_learned(float *__restrict__ g, const StepArgs<float> a,
                                                          const LearnArgs L)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
@@ -30,13 +32,17 @@ __global__ void __launch_bounds__(128, 4) k_step_learned(float *__restrict__ g, 
 #pragma unroll
     for (int s = 0; s < NSTAT; ++s) acc[s] = 0.0f;
     const I N = I(a.n);
-    for (uint64_t ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x) {
+    const uint64_t nsuper = (a.nchunks + kMlpSub - 1) / kMlpSub;
+    for (uint64_t sc = blockIdx.x; sc < nsuper; sc += gridDim.x) {
+        const uint64_t ch0 = sc * kMlpSub + (threadIdx.x >> 7);
+        const bool live = ch0 < a.nchunks;
+        const uint64_t ch = live ? ch0 : 0;
         const uint32_t xc = uint32_t(ch % a.cpr);
         const uint64_t r = ch / a.cpr;
         const uint32_t y = uint32_t(r % a.ny);
         const uint32_t z = uint32_t(r / a.ny);
-        const uint32_t x = xc * 128 + threadIdx.x;
-        const bool active = x < a.nx;
+        const uint32_t x = xc * 128 + (threadIdx.x & 127u);
+        const bool active = live && x < a.nx;
         const Nbr<I> nb(active ? x : 0, y, z, a.nx, a.ny, a.nz);
         const I n = nb.node();
         float v[3][3][3];
@@ -113,11 +119,11 @@ cudaError_t launch_t(float *g, const StepArgs<float> &a, const LearnArgs &L, boo
                      cudaStream_t s)
 {
     if (odd) {
-        if (stats) k_step_learned<I, true, true><<<grid, 128, kMlpSmemBytes, s>>>(g, a, L);
-        else k_step_learned<I, true, false><<<grid, 128, kMlpSmemBytes, s>>>(g, a, L);
+        if (stats) k_step_learned<I, true, true><<<grid, kMlpThreads, kMlpSmemBytes, s>>>(g, a, L);
+        else k_step_learned<I, true, false><<<grid, kMlpThreads, kMlpSmemBytes, s>>>(g, a, L);
     } else {
-        if (stats) k_step_learned<I, false, true><<<grid, 128, kMlpSmemBytes, s>>>(g, a, L);
-        else k_step_learned<I, false, false><<<grid, 128, kMlpSmemBytes, s>>>(g, a, L);
+        if (stats) k_step_learned<I, false, true><<<grid, kMlpThreads, kMlpSmemBytes, s>>>(g, a, L);
+        else k_step_learned<I, false, false><<<grid, kMlpThreads, kMlpSmemBytes, s>>>(g, a, L);
     }
     return cudaGetLastError();
 }
@@ -135,7 +141,7 @@ cudaError_t launch_step_learned(float *g, const StepArgs<float> &a, const LearnA
 
 int learned_occupancy(uint64_t n)
 {
-    // static (reduction) + dynamic shared memory exceed the 48 KB default
+    // the sub-tile buffers exceed the 48 KB default
     const int sm = int(kMlpSmemBytes);
     cudaFuncSetAttribute(k_step_learned<uint32_t, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_step_learned<uint32_t, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -147,10 +153,13 @@ int learned_occupancy(uint64_t n)
     cudaFuncSetAttribute(k_step_learned<uint64_t, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     int nb = 0;
     const cudaError_t e = fits32(n)
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_learned<uint32_t, true, true>, 128, kMlpSmemBytes)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_learned<uint64_t, true, true>, 128, kMlpSmemBytes);
-    if (e != cudaSuccess || nb < 1) return 1;
-    return nb < 4 ? nb : 4;   // 128 tensor-memory columns per CTA, 512 per SM
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_learned<uint32_t, true, true>, kMlpThreads,
+                                                        kMlpSmemBytes)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_learned<uint64_t, true, true>, kMlpThreads,
+                                                        kMlpSmemBytes);
+    (void)nb;
+    (void)e;
+    return 1;   // a CTA holds all 512 tensor-memory columns of its SM
 }
 
 }  // namespace flbm
