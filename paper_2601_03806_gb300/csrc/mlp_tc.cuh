@@ -14,8 +14,11 @@
 //   h2 = silu(D2 + b2) as bf16                               -> A2 again
 //   D3 = h2 W3^T  (N 32, K 64: four MMAs; rows 27..31 of W3 are zero) -> cols 0..31
 //   y = D3 + b3                                              -> thread t's registers
-// One elected thread issues the MMAs of all four sub-tiles; their completion
-// arrives on one mbarrier that every thread waits on (bounded).  The weight
+// Each sub-tile is an independent group of 4 warps (128 threads) with its
+// own named barrier (id 1 + group), its own mbarrier and its own MMA issuer,
+// so the groups drift out of phase and one group's epilogue fills another's
+// MMA latency -- what separate CTAs would do if the SM granted them.  Every
+// wait is bounded, and its outcome is made uniform over the group.  The weight
 // image (bf16, already in the operand layout of umma.cuh) and the FP32
 // biases are copied into shared memory once per CTA.
 #pragma once
@@ -41,7 +44,7 @@ struct MlpSmem {
     float bias[64 + 64 + 32];                          // b1 | b2 | b3 (b3 zero-padded)
     __align__(128) unsigned char a1[kMlpSub][128 * 32 * 2];
     __align__(128) unsigned char a2[kMlpSub][128 * 64 * 2];
-    uint64_t bar;
+    uint64_t bar[kMlpSub];
     uint32_t tmem;
 };
 constexpr size_t kMlpSmemBytes = (sizeof(MlpSmem) + 1023) / 1024 * 1024;
@@ -86,7 +89,7 @@ __device__ __forceinline__ void mlp_setup(MlpSmem &sm, const unsigned char *__re
     const float *bsrc = reinterpret_cast<const float *>(img + kBiasOff);
     for (uint32_t i = threadIdx.x; i < 160; i += blockDim.x) sm.bias[i] = bsrc[i];
     if (threadIdx.x == 0) {
-        mbar_init(&sm.bar, 1);
+        for (uint32_t q = 0; q < kMlpSub; ++q) mbar_init(&sm.bar[q], 1);
         mbar_init_fence();
     }
     if (threadIdx.x < 32) tmem_alloc(&sm.tmem, kMlpTmemCols);
@@ -104,22 +107,40 @@ __device__ __forceinline__ void mlp_teardown(MlpSmem &sm)
     if (threadIdx.x < 32) tmem_dealloc(sm.tmem, kMlpTmemCols);
 }
 
-// Wait for the MMAs committed to sm.bar; the outcome is made uniform over the
-// CTA so that no thread leaves the tile loop alone.
-__device__ __forceinline__ bool mlp_wait(MlpSmem &sm, uint32_t &phase)
+// Barrier of the 128 threads of group q (named barrier 1 + q).
+__device__ __forceinline__ void group_sync(uint32_t q)
 {
-    const bool ok = mbar_wait(&sm.bar, phase);
+    asm volatile("bar.sync %0, 128;\n" ::"r"(1u + q) : "memory");
+}
+// The same barrier, returning whether pred held on every thread of the group.
+__device__ __forceinline__ bool group_all(uint32_t q, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, o;\n setp.ne.u32 p, %1, 0;\n"
+        " bar.red.and.pred o, %2, 128, p;\n selp.u32 %0, 1, 0, o;\n}\n"
+        : "=r"(r)
+        : "r"(uint32_t(pred)), "r"(1u + q)
+        : "memory");
+    return r != 0;
+}
+
+// Wait for the MMAs committed to the group's mbarrier; the outcome is made
+// uniform over the group so that no thread leaves the loop alone.
+__device__ __forceinline__ bool mlp_wait(MlpSmem &sm, uint32_t q, uint32_t &phase)
+{
+    const bool ok = mbar_wait(&sm.bar[q], phase);
     phase ^= 1u;
-    const bool all = __syncthreads_and(ok) != 0;
+    const bool all = group_all(q, ok);
     tc_fence_after();
     return all;
 }
 
-__device__ __forceinline__ void mlp_sync_for_mma()
+__device__ __forceinline__ void mlp_sync_for_mma(uint32_t q)
 {
     fence_proxy_async_smem();   // generic-proxy operand writes before the MMAs read them
     tc_fence_before();          // earlier tensor-memory reads before the MMAs overwrite
-    __syncthreads();
+    group_sync(q);
 }
 
 // One round: x = this thread's 28 features (row t % 128 of sub-tile t / 128),
@@ -145,20 +166,18 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
         for (int i = 0; i < 16; ++i) v[i] = (16 + i < kMlpIn) ? x[16 + i] : 0.0f;
         store_row16(a1p, kSbo32, t, 16, v);
     }
-    mlp_sync_for_mma();
-    if (threadIdx.x == 0) {
+    mlp_sync_for_mma(q);
+    if (t == 0) {
         tc_fence_after();
-        for (uint32_t qq = 0; qq < kMlpSub; ++qq) {
-            const uint32_t a1 = smem_u32(sm.a1[qq]);
+        const uint32_t a1 = smem_u32(a1p);
 #pragma unroll
-            for (uint32_t s = 0; s < 2; ++s)
-                umma_bf16(sm.tmem + 128u * qq, umma_smem_desc(a1 + 256 * s, 128, kSbo32),
-                          umma_smem_desc(w + kW1Off + 256 * s, 128, kSbo32), idesc64, s > 0);
-        }
-        umma_commit(&sm.bar);
+        for (uint32_t s = 0; s < 2; ++s)
+            umma_bf16(tmem, umma_smem_desc(a1 + 256 * s, 128, kSbo32),
+                      umma_smem_desc(w + kW1Off + 256 * s, 128, kSbo32), idesc64, s > 0);
+        umma_commit(&sm.bar[q]);
     }
     work();
-    bool ok = mlp_wait(sm, phase);
+    bool ok = mlp_wait(sm, q, phase);
     if (ok) {
 #pragma unroll
         for (uint32_t ch = 0; ch < 4; ++ch) {
@@ -168,19 +187,17 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
             for (int i = 0; i < 16; ++i) z[i] = silu_fast(z[i] + sm.bias[16 * ch + i]);
             store_row16(a2p, kSbo64, t, 16 * ch, z);
         }
-        mlp_sync_for_mma();
-        if (threadIdx.x == 0) {
+        mlp_sync_for_mma(q);
+        if (t == 0) {
             tc_fence_after();
-            for (uint32_t qq = 0; qq < kMlpSub; ++qq) {
-                const uint32_t a2 = smem_u32(sm.a2[qq]);
+            const uint32_t a2 = smem_u32(a2p);
 #pragma unroll
-                for (uint32_t s = 0; s < 4; ++s)
-                    umma_bf16(sm.tmem + 128u * qq + 64, umma_smem_desc(a2 + 256 * s, 128, kSbo64),
-                              umma_smem_desc(w + kW2Off + 256 * s, 128, kSbo64), idesc64, s > 0);
-            }
-            umma_commit(&sm.bar);
+            for (uint32_t s = 0; s < 4; ++s)
+                umma_bf16(tmem + 64, umma_smem_desc(a2 + 256 * s, 128, kSbo64),
+                          umma_smem_desc(w + kW2Off + 256 * s, 128, kSbo64), idesc64, s > 0);
+            umma_commit(&sm.bar[q]);
         }
-        ok = mlp_wait(sm, phase);
+        ok = mlp_wait(sm, q, phase);
     }
     if (ok) {
 #pragma unroll
@@ -191,19 +208,17 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
             for (int i = 0; i < 16; ++i) z[i] = silu_fast(z[i] + sm.bias[64 + 16 * ch + i]);
             store_row16(a2p, kSbo64, t, 16 * ch, z);
         }
-        mlp_sync_for_mma();
-        if (threadIdx.x == 0) {
+        mlp_sync_for_mma(q);
+        if (t == 0) {
             tc_fence_after();
-            for (uint32_t qq = 0; qq < kMlpSub; ++qq) {
-                const uint32_t a2 = smem_u32(sm.a2[qq]);
+            const uint32_t a2 = smem_u32(a2p);
 #pragma unroll
-                for (uint32_t s = 0; s < 4; ++s)
-                    umma_bf16(sm.tmem + 128u * qq, umma_smem_desc(a2 + 256 * s, 128, kSbo64),
-                              umma_smem_desc(w + kW3Off + 256 * s, 128, kSbo64), idesc32, s > 0);
-            }
-            umma_commit(&sm.bar);
+            for (uint32_t s = 0; s < 4; ++s)
+                umma_bf16(tmem, umma_smem_desc(a2 + 256 * s, 128, kSbo64),
+                          umma_smem_desc(w + kW3Off + 256 * s, 128, kSbo64), idesc32, s > 0);
+            umma_commit(&sm.bar[q]);
         }
-        ok = mlp_wait(sm, phase);
+        ok = mlp_wait(sm, q, phase);
     }
     if (ok) {
 #pragma unroll
@@ -217,7 +232,7 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
         return true;
     }
     // a wait ran out: give the MMAs in flight one more bounded wait
-    mbar_wait(&sm.bar, phase);
+    mbar_wait(&sm.bar[q], phase);
     return false;
 }
 
