@@ -256,3 +256,40 @@ def test_learned_equipartition_and_flat_spectrum(F, M, torch_cuda):
         assert np.all(np.abs(u2 - 1) < 0.02), (scheme, u2)
         assert abs(s - 1) < 0.03, (scheme, s)
     assert np.all(np.abs(out[F.FLBM_LEARNED][0] - out[F.FLBM_GMF][0]) < 0.01)
+
+
+def test_learned_step_full_size_sampled_nodes(F, M, oracle_mod):
+    """The 256^3 learned box in the benchmark's launch shape: one learned step
+    minus one GMF step from the same state and noise, at 48 sampled nodes
+    (all 27 directions, read where streaming put them) against the oracle's
+    correction of the probed pre-collision populations.  kT = 1e-3 keeps the
+    correction above FP32 rounding; the bound is the propagated one."""
+    O = oracle_mod
+    n, tau, kT, rho0 = 256, 0.8, 1e-3, 1.0
+    theta = random_net(M, 33)
+    boxes = {}
+    for scheme in (F.FLBM_GMF, F.FLBM_LEARNED):
+        b = F.Lattice(n, n, n, tau, kT, rho0=rho0, seed=21, scheme=scheme)
+        b.init_thermal(5)
+        boxes[scheme] = b
+    boxes[F.FLBM_LEARNED].set_mlp(theta)
+    c = O.tables()["c"]
+    w = O.tables()["w"]
+    rng = np.random.default_rng(0)
+    pts = rng.integers(0, n, size=(48, 3))
+    pts[0] = (0, 0, 0)
+    pts[1] = (n - 1, n - 1, n - 1)
+    node = lambda x, y, z: int(x % n + n * ((y % n) + n * (z % n)))
+    pre = boxes[F.FLBM_LEARNED].probe([node(*p) for p in pts])          # [48, 27]
+    for b in boxes.values():
+        b.step(1)
+    dst = [node(x + c[i, 0], y + c[i, 1], z + c[i, 2]) for (x, y, z) in pts for i in range(27)]
+    post = {s: b.probe(dst).reshape(48, 27, 27) for s, b in boxes.items()}
+    idx = np.arange(27)
+    D = post[F.FLBM_LEARNED][:, idx, idx] - post[F.FLBM_GMF][:, idx, idx]
+    corr = M.correction(theta, pre, rho0, kT, 1.0 / tau, bf16=True)
+    _, ey = bound(M, theta, M.features(pre, rho0, kT, 1.0 / tau))
+    dlt = w * (kT / rho0) ** 1.5 * ey
+    eb = dlt + w * (1 + 3 * np.abs(c).sum(1)) * dlt.sum(1, keepdims=True) + 1e-8
+    assert np.all(np.abs(D - corr) <= eb), (np.abs(D - corr).max(), (np.abs(D - corr) / eb).max())
+    assert np.abs(corr).max() > 1e-6
