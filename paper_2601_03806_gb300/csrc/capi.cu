@@ -330,8 +330,9 @@ int flbm::create_ctx(const flbm_params *p, void *dev_buf, size_t dev_bytes, void
     c->grid = int(std::min<uint64_t>(nchunks, uint64_t(c->nsm) * per_sm));
     if (c->grid < 1) c->grid = 1;
     // FLBM_INJECT_STARVE=1 (environment, failure-injection tests only): the
-    // row pipeline expects 16 bytes more than it copies, so its bounded waits
-    // run out and flbm_step reports FLBM_E_TIMEOUT
+    // row pipeline expects 16 bytes more than it copies (the learned step
+    // never commits its first network layer), so the bounded waits run out
+    // and flbm_step reports FLBM_E_TIMEOUT
     if (const char *inj = std::getenv("FLBM_INJECT_STARVE"))
         if (std::atoi(inj) == 1) c->tx_pad = 16;
     // FLBM_ROWS=0 (environment) disables the TMA row pipeline
@@ -432,6 +433,7 @@ int flbm_step(flbm_ctx *c, int64_t n)
             for (int k = 0; k < 4; ++k) L.inv_s[k] = float(1.0 / std::sqrt(c->p.rho0 * c->p.kT * w[k] * 3.0));
             L.sig3 = float(std::pow(c->p.kT / c->p.rho0, 1.5));
             L.x27 = float(1.0 / c->p.tau - 1.0);
+            L.starve = c->tx_pad != 0;   // FLBM_INJECT_STARVE=1 (tests)
             e = launch_step_learned(static_cast<float *>(c->g), make_args<float>(c, t), L, odd, stats, c->grid,
                                     c->stream);
         } else if (c->p.precision == FLBM_FP64)

@@ -165,6 +165,7 @@ struct LearnArgs {
     float inv_s[4];             // 1 / sqrt(rho0 kT w / c_s^2) for |c|^2 = 0, 1, 2, 3
     float sig3;                 // (kT / rho0)^(3/2)
     float x27;                  // omega - 1
+    int32_t starve;             // failure injection (tests): never commit layer 1
 };
 cudaError_t launch_step_learned(float *g, const StepArgs<float> &a, const LearnArgs &L, bool odd, bool stats,
                                 int grid, cudaStream_t s);

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_infer(const float *__res
         for (int i = 0; i < kMlpIn; ++i) xr[i] = row < n ? x[row * kMlpIn + i] : 0.0f;
         float yr[kMlpOut];
         if (!mlp_tile(sm, phase, xr, yr, [] {})) {
-            if (threadIdx.x == 0) atomicOr(flag, 2u);
+            if ((threadIdx.x & 127u) == 0) atomicOr(flag, 2u);   // one report per group
             break;
         }
         if (row < n)

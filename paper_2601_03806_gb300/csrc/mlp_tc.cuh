@@ -146,10 +146,12 @@ __device__ __forceinline__ void mlp_sync_for_mma(uint32_t q)
 // One round: x = this thread's 28 features (row t % 128 of sub-tile t / 128),
 // y = its 27 outputs.  work() runs while the first layer's MMAs are in flight.  Returns
 // false (on every thread) if a wait ran out; the MMAs are then drained with
-// one more bounded wait before returning.
+// one more bounded wait before returning.  starve (failure injection, tests
+// only): the first layer's completion is never committed, so the waits run
+// out.
 template <typename Work>
 __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const float (&x)[kMlpIn],
-                                         float (&y)[kMlpOut], Work &&work)
+                                         float (&y)[kMlpOut], Work &&work, bool starve = false)
 {
     const uint32_t t = threadIdx.x & 127u, q = threadIdx.x >> 7;
     const uint32_t tmem = sm.tmem + 128u * q;                 // this sub-tile's columns
@@ -174,7 +176,7 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
         for (uint32_t s = 0; s < 2; ++s)
             umma_bf16(tmem, umma_smem_desc(a1 + 256 * s, 128, kSbo32),
                       umma_smem_desc(w + kW1Off + 256 * s, 128, kSbo32), idesc64, s > 0);
-        umma_commit(&sm.bar[q]);
+        if (!starve) umma_commit(&sm.bar[q]);
     }
     work();
     bool ok = mlp_wait(sm, q, phase);

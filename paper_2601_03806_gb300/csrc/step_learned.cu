@@ -65,9 +65,9 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_step_learned(float *__restri
         float nzd[kNoise];   // unused: the collision draws its normals inside
         const bool ok = mlp_tile(sm, phase, xf, yv, [&] {
             if (active) collide_core<float, 1, STATS, false>(v, a, nzd, uint32_t(n), acc);
-        });
+        }, L.starve != 0);
         if (!ok) {
-            if (threadIdx.x == 0) atomicOr(a.flag, 2u);
+            if ((threadIdx.x & 127u) == 0) atomicOr(a.flag, 2u);   // one report per group
             break;
         }
         if (!active) continue;

@@ -31,3 +31,28 @@ def test_row_pipeline_wait_runs_out_and_reports_timeout(monkeypatch):
     h = flbm.Lattice(64, 4, 3, 0.8, 1e-5, precision=flbm.FLBM_FP32)
     h.step(3)
     assert abs(h.stats()["mass"] / (64 * 4 * 3) - 1) < 1e-6
+
+
+def test_learned_step_tensor_core_wait_runs_out_and_reports_timeout(monkeypatch):
+    """FLBM_INJECT_STARVE=1 on a learned-scheme context: the network's first
+    layer is never committed to its mbarrier, every group's bounded wait runs
+    out (about a second, plus one drain wait), the step returns
+    FLBM_E_TIMEOUT and the device stays usable."""
+    from paper_2601_03806_gb300 import flbm
+    import numpy as np
+    theta = np.zeros(flbm.MLP_NPARAM, np.float32)
+    monkeypatch.setenv("FLBM_INJECT_STARVE", "1")
+    g = flbm.Lattice(128, 4, 4, 0.8, 1e-4, scheme=flbm.FLBM_LEARNED)
+    monkeypatch.delenv("FLBM_INJECT_STARVE")
+    g.set_mlp(theta)
+    t0 = time.time()
+    with pytest.raises(flbm.FlbmError) as ei:
+        g.step(1)
+    assert ei.value.code == flbm.FLBM_E_TIMEOUT
+    assert time.time() - t0 < 30
+    g.close()
+    h = flbm.Lattice(128, 4, 4, 0.8, 1e-4, scheme=flbm.FLBM_LEARNED)
+    h.set_mlp(theta)
+    h.init_thermal(2)
+    h.step(3)
+    assert abs(h.stats()["mass"] / (128 * 16) - 1) < 1e-2
