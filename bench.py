@@ -63,6 +63,8 @@ def parse_args(argv=None):
     ap.add_argument("--train-boxes", type=int, default=64,
                     help="learned: Reg-FLBM 64^3 boxes whose pairs train the network (64 = 2^24 pairs)")
     ap.add_argument("--train-epochs", type=int, default=6)
+    ap.add_argument("--stat-steps", type=int, default=5000,
+                    help="learned: steps of the statistics run after the timed region (0: skip)")
     ap.add_argument("--ens-div", type=int, default=1,
                     help="ensemble: divide every replica count by this (profiling runs; 1 = the "
                          "benchmark workload)")
@@ -701,6 +703,29 @@ def run_learned(args, rank, local, ws):
         st = lat.stats()
         return lat, el, kms / max(launches, 1), launches, clk.summary(), st
 
+    from paper_2601_03806_gb300 import analysis
+
+    def statistics(lat):
+        """Config-5 judgement: equipartition (time average over the run) and
+        the S(k) spectra (mean over 10 snapshots) against their flat theory."""
+        if args.stat_steps <= 0:
+            return None
+        lat.stats_reset()
+        obs = analysis.PAPER_OBSERVABLES + (flbm.FLBM_OBS_JX,)
+        names = {flbm.FLBM_OBS_RHO: "rho", flbm.FLBM_OBS_JSUM: "j_sum", flbm.FLBM_OBS_PI_DIAG: "pi_diag",
+                 flbm.FLBM_OBS_PI_OFFDIAG: "pi_offdiag", flbm.FLBM_OBS_JX: "jx"}
+        er = analysis.er_spectrum(lat, n // 2, snapshots=10, every=max(1, args.stat_steps // 10), observables=obs)
+        stt = lat.stats()
+        out = {"steps": 10 * max(1, args.stat_steps // 10),
+               "u2_avg_over_kT_rho0": [x / (kT / rho0) for x in stt["u2_avg"]], "er": stt["er"]}
+        for m in obs:
+            ratio, cnt = er[m]
+            k = cnt > 0
+            lo, hi = analysis.window_extrema(ratio, cnt, 4, n // 2 - 1)
+            out["S_" + names[m] + "_over_theory"] = {"mean": float(np.sum(ratio[k] * cnt[k]) / np.sum(cnt[k])),
+                                                      "min_shell_4_up": lo, "max_shell_4_up": hi}
+        return out
+
     lat, el_ms, k_ms, launches, clocks, st = timed(flbm.FLBM_LEARNED)
     max_ms = max_over_ranks(el_ms, ws, dev)
     value = job_mlups(N, args.steps, max_ms, ws)
@@ -739,8 +764,10 @@ def run_learned(args, rank, local, ws):
                "d2h_bytes_per_step": ctypes.sizeof(flbm.flbm_stats_t) + 16,
                "what": "flbm_set_state from pinned host + K x (flbm_step(1) + flbm_stats)"}
         del hstate
+    stats_learned = statistics(lat)
     lat.close()
     glat, gel, gk_ms, _, _, gst = timed(flbm.FLBM_GMF)
+    stats_gmf = statistics(glat)
     glat.close()
     plain = {"value": job_mlups(N, args.steps, max_over_ranks(gel, ws, dev), ws), "unit": "MLUPS",
              "what": "plain GMF-FLBM (row pipeline) on the same box",
@@ -785,6 +812,7 @@ def run_learned(args, rank, local, ws):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain_kernel": plain,
             "gpu_launches": int(launches) + int(args.steps), "clocks": clocks,
             "training": training,
+            "statistics": {"learned": stats_learned, "gmf": stats_gmf},
             "equipartition": {"u2_avg_over_kT_rho0": u2, "max_abs_error": max(abs(x - 1) for x in u2),
                               "samples": st["n_samples"]},
         }
