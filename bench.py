@@ -64,7 +64,7 @@ def parse_args(argv=None):
                     help="learned: Reg-FLBM 64^3 boxes whose pairs train the network (64 = 2^24 pairs)")
     ap.add_argument("--train-epochs", type=int, default=6)
     ap.add_argument("--stat-steps", type=int, default=5000,
-                    help="learned: steps of the statistics run after the timed region (0: skip)")
+                    help="learned, ensemble: steps of the statistics run after the timed region (0: skip)")
     ap.add_argument("--ens-div", type=int, default=1,
                     help="ensemble: divide every replica count by this (profiling runs; 1 = the "
                          "benchmark workload)")
@@ -533,18 +533,34 @@ def run_ensemble(args, rank, local, ws):
                           "time of both, graph replay)",
                 "kernel_ms": step_ms, "algorithmic_bytes_per_launch": BYTES_PER_NODE["fp32"] * N}
 
-    # ensemble-averaged <u_a^2> per replica and S(k) flatness per box size
+    # statistics run (config 4: 5000 steps): ensemble-averaged <u_a^2> of
+    # every replica, and the S_jx(k) flatness of every replica (mean over
+    # the run's snapshots), summarised per box size
+    stat_steps = args.stat_steps if args.stat_steps > 0 else args.steps
+    for rep in ens.replicas:
+        rep.stats_reset()
+    snaps, every = (10, max(1, stat_steps // 10)) if args.stat_steps > 0 else (1, args.steps)
+    sacc = [None] * len(ens.replicas)
+    for _ in range(snaps):
+        ens.step(every)
+        for r, rep in enumerate(ens.replicas):
+            S, cnt = rep.structure_factor(flbm.FLBM_OBS_JX, sizes[r] // 2)
+            m = cnt > 0
+            v = float(np.sum(S[m] * cnt[m]) / np.sum(cnt[m]) / (rho0 * kT))
+            sacc[r] = v if sacc[r] is None else sacc[r] + v
     u2 = np.array([rep.stats()["u2_avg"] for rep in ens.replicas]) / (kT / rho0)
-    sk = {}
+    sk = np.array(sacc) / snaps
+    per_size = {}
     for n in sorted(set(sizes)):
-        r = sizes.index(n)
-        S, cnt = ens[r].structure_factor(flbm.FLBM_OBS_JX, n // 2)
-        m = cnt > 0
-        sk["%d^3" % n] = float(np.sum(S[m] * cnt[m]) / np.sum(cnt[m]) / (rho0 * kT))
-    equip = {"u2_avg_over_kT_rho0_mean": float(u2.mean()),
+        idx = [r for r, m in enumerate(sizes) if m == n]
+        per_size["%d^3" % n] = {"replicas": len(idx),
+                                "u2_mean": float(u2[idx].mean()),
+                                "u2_max_abs_error": float(np.abs(u2[idx] - 1).max()),
+                                "S_jx_mean": float(sk[idx].mean()),
+                                "S_jx_max_abs_error": float(np.abs(sk[idx] - 1).max())}
+    equip = {"steps": snaps * every, "u2_avg_over_kT_rho0_mean": float(u2.mean()),
              "max_abs_error_over_replicas": float(np.abs(u2 - 1).max()),
-             "samples_per_replica": args.steps,
-             "S_jx_mean_over_rho0_kT_first_replica_of_each_size": sk}
+             "S_jx_over_rho0_kT_mean": float(sk.mean()), "per_size": per_size}
 
     # the same replicas as independent boxes, one plain flbm_step call each
     plain = None
