@@ -251,6 +251,24 @@ def oracle_sample(tau, kT, rho0, seed, budget_s=2.0, n=64):
     return n ** 3 * steps / el / 1e6, threads, steps, [float(x) for x in u2]
 
 
+def oracle_single_thread(tau, kT, rho0, seed, budget_s=1.0, n=32):
+    """The oracle on one host thread (MLUPS), a bounded sample."""
+    import oracle
+    oracle.build()
+    prev = oracle.get_threads()
+    oracle.set_threads(1)
+    box = oracle.Box(n, n, n, tau, kT, rho0=rho0, seed=seed)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        box.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s and steps >= 2:
+            break
+    oracle.set_threads(prev)
+    return n ** 3 * steps / el / 1e6
+
+
 def run_reference(args, rank, ws):
     if rank != 0:
         return 0
@@ -417,6 +435,7 @@ def run_ours(args, rank, local, ws):
         cpu = {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
                "sample": "64^3 box with the workload's tau/kT/rho0 from a thermal state, %d steps, "
                          "FP64 two-array oracle on %d host threads" % (steps, threads),
+               "single_thread_value": oracle_single_thread(tau, kT, rho0, WORKLOAD["seed"]),
                "u2_ratio": u2o}
 
     if rank == 0:

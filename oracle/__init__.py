@@ -7,7 +7,8 @@ calls it; it shares no code, header or table with the CUDA path.
 Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
 
 * ``tables``            pinned: Table II printed b_k, orthogonality, n_k/mu_k relation
-* ``philox4x32_10``     pinned: published known-answer vectors (Salmon et al. SC'11)
+* ``philox4x32_10``     pinned: published known-answer vectors (Salmon et al. SC'11),
+                        and cuRAND's Philox4_32_10 on 202 counters/keys (GPU test)
 * ``normals``           pinned: moments of the normal stream; Box-Muller identity
 * ``feq2``              pinned: moments 0/1/2 exact, zero ghost projection
 * ``noise_term``        pinned: conservation, single-node AR(1) stationary variance
