@@ -143,7 +143,8 @@ int flbm_create(int nx, int ny, int nz, double tau, double kT, double rho0,
  * least flbm_state_bytes(p) bytes, 256-byte aligned, that the caller (e.g.
  * PyTorch) owns and keeps alive; cuda_stream: NULL for a library-owned
  * stream, else a cudaStream_t on the current device that all work of this
- * context is ordered on. */
+ * context is ordered on.  FLBM_E_INVALID if dev_buf is not device (or
+ * managed) memory. */
 int flbm_create_ex(const flbm_params *p, void *dev_buf, size_t dev_bytes,
                    void *cuda_stream, flbm_ctx **out);
 
@@ -379,7 +380,8 @@ int flbm_mlp_infer(const float *params, const float *x, int64_t n, float *y);
  * (Reg-FLBM, this library's reading: unit ghost relaxation towards the
  * full-order equilibrium) differs from the GMF collision of the same
  * pre-collision state, in units of the network output.  Computed in FP64,
- * stored as FP32.  Needs kT > 0.  Node n = x + nx (y + ny z). */
+ * stored as FP32.  Needs kT > 0.  Node n = x + nx (y + ny z).  Host
+ * pointers are rejected with FLBM_E_INVALID (as by flbm_mlp_grad/train). */
 int flbm_mlp_pairs(flbm_ctx *c, float *dev_x, float *dev_t);
 
 /* Gradient of L = mean over the n samples and 27 outputs of (y - t)^2 with

@@ -59,6 +59,18 @@ int prec_code(const flbm_ctx *c) { return c->p.precision == FLBM_FP64 ? 0 : (c->
 
 int parity(const flbm_ctx *c) { return int((c->step + c->phase) & 1); }
 
+// Whether p is memory the device can address as global memory (device or
+// managed); a host pointer handed to a kernel would fault instead of failing.
+bool is_device_memory(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the query's error
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 BoxDesc box_of(const flbm_ctx *c)
 {
     BoxDesc b;
@@ -299,6 +311,10 @@ int flbm::create_ctx(const flbm_params *p, void *dev_buf, size_t dev_bytes, void
         }
         if (reinterpret_cast<uintptr_t>(dev_buf) % 256 != 0) {
             c->err = "dev_buf must be 256-byte aligned";
+            return bail(FLBM_E_INVALID);
+        }
+        if (!is_device_memory(dev_buf)) {
+            c->err = "dev_buf must be device (or managed) memory";
             return bail(FLBM_E_INVALID);
         }
         c->g = dev_buf;
@@ -736,6 +752,8 @@ int flbm_mlp_pairs(flbm_ctx *c, float *dev_x, float *dev_t)
 {
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
     if (!dev_x || !dev_t) return fail(c, FLBM_E_INVALID, "dev_x and dev_t must not be NULL");
+    if (!is_device_memory(dev_x) || !is_device_memory(dev_t))
+        return fail(c, FLBM_E_INVALID, "dev_x and dev_t must be device (or managed) memory");
     if (!(c->p.kT > 0.0)) return fail(c, FLBM_E_INVALID, "training pairs need kT > 0 (the feature scale)");
     int rc = ensure_pipe(c);
     if (rc) return rc;

@@ -284,6 +284,18 @@ int fail(const std::string &m, int code)
     return code;
 }
 
+// Whether p is device (or managed) memory; a host pointer handed to a
+// kernel would fault instead of failing.
+bool is_device_memory(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 int prepare(Scratch &sc, const float *params, int &nsm, bool adam)
 {
     int dev = 0;
@@ -343,6 +355,8 @@ extern "C" int flbm_mlp_grad(const float *params, const float *dev_x, const floa
 {
     if (!params || !dev_x || !dev_t || !grad || n < 1 || n >= (int64_t(1) << 32))
         return fail("flbm_mlp_grad: NULL argument or n outside [1, 2^32)", FLBM_E_INVALID);
+    if (!is_device_memory(dev_x) || !is_device_memory(dev_t))
+        return fail("flbm_mlp_grad: dev_x and dev_t must be device (or managed) memory", FLBM_E_INVALID);
     Scratch sc;
     int nsm = 0;
     int rc = prepare(sc, params, nsm, false);
@@ -363,6 +377,8 @@ extern "C" int flbm_mlp_train(float *params, const float *dev_x, const float *de
     if (!params || !dev_x || !dev_t || n < 1 || n >= (int64_t(1) << 32) || epochs < 1 || batch < 1 ||
         !(lr > 0.0) || !std::isfinite(lr))
         return fail("flbm_mlp_train: bad argument", FLBM_E_INVALID);
+    if (!is_device_memory(dev_x) || !is_device_memory(dev_t))
+        return fail("flbm_mlp_train: dev_x and dev_t must be device (or managed) memory", FLBM_E_INVALID);
     Scratch sc;
     int nsm = 0;
     int rc = prepare(sc, params, nsm, true);

@@ -156,3 +156,18 @@ def test_null_context_calls_are_rejected(F):
     assert F.flbm_get_step(None) == -1
     assert F.flbm_stats_reset(None) == F.FLBM_E_INVALID
     F.flbm_destroy(None)
+
+
+def test_mlp_calls_reject_host_pointers(F):
+    """Device-array arguments must be device memory: a host array is
+    rejected before any kernel could fault on it (the query needs no GPU:
+    without a device it fails, which is rejected the same way)."""
+    import numpy as np
+    p = np.zeros(F.MLP_NPARAM, np.float32)
+    x = np.zeros((4, 28), np.float32)
+    t = np.zeros((4, 27), np.float32)
+    g = np.zeros(F.MLP_NPARAM, np.float32)
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)
+    assert F.flbm_mlp_grad(ptr(p), ptr(x), ptr(t), 4, ptr(g), None) == F.FLBM_E_INVALID
+    assert F.flbm_mlp_train(ptr(p), ptr(x), ptr(t), 4, 1, 4, 1e-3, 0, None) == F.FLBM_E_INVALID
+    assert b"device" in F.flbm_last_error(None)
