@@ -213,6 +213,28 @@ def recorded_traffic(nodes: int, path=None, sources=None):
         return None
 
 
+def bind_to_gpu_numa_node(torch, dev) -> str:
+    """Run this process on the CPUs local to the GPU, so that pinned host
+    buffers allocated afterwards sit next to it (host<->device copies cross
+    no socket link).  Returns what was done, for the JSON line."""
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        bus = "%04x:%02x:%02x.0" % (getattr(p, "pci_domain_id", 0), p.pci_bus_id, p.pci_device_id)
+        base = "/sys/bus/pci/devices/" + bus
+        cpus = open(base + "/local_cpulist").read().strip()
+        sel = set()
+        for part in cpus.split(","):
+            a, _, b = part.partition("-")
+            sel.update(range(int(a), int(b or a) + 1))
+        sel &= os.sched_getaffinity(0)
+        if not sel:
+            return "not bound (no local CPUs available)"
+        os.sched_setaffinity(0, sel)
+        return "bound to the %d CPUs local to GPU %s" % (len(sel), bus)
+    except Exception as e:
+        return "not bound (%s)" % type(e).__name__
+
+
 def host_mem_available() -> int:
     try:
         for ln in open("/proc/meminfo"):
@@ -389,6 +411,7 @@ def run_ours(args, rank, local, ws):
     # each followed by a stats read, then one moments snapshot to the host.
     e2e = None
     if not args.no_e2e:
+        numa = bind_to_gpu_numa_node(torch, dev)
         state_bytes = 27 * es * N
         mom_bytes = 10 * 8 * N
         with_moments = host_mem_available() > 3 * (state_bytes + mom_bytes)
@@ -426,7 +449,7 @@ def run_ours(args, rank, local, ws):
                "d2h_bytes_per_step": (mom_bytes if with_moments else 0) // args.steps + stats_bytes,
                "what": "flbm_set_state from pinned host + K x (flbm_step(1) + flbm_stats)"
                        + (" + flbm_moments snapshot to pinned host" if with_moments else ""),
-               "split": e2e_split}
+               "split": e2e_split, "host_placement": numa}
         del hstate
 
     cpu = None
