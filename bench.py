@@ -188,11 +188,39 @@ def measured_hbm_peak():
         return 6800.0, "of fallback"
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments, trailing blanks and empty lines
+    (string and character literals are kept), so that the hash below
+    follows the code and not its commentary."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = (ln.rstrip() for ln in "".join(out).split("\n"))
+    return "\n".join(ln for ln in lines if ln)
+
+
 def kernel_source_hash(sources=None) -> str:
+    """sha256 (first 16 hex digits) of the kernel sources, comments left out."""
     h = hashlib.sha256()
     for f in (KERNEL_SOURCES if sources is None else sources):
-        with open(os.path.join(ROOT, "paper_2601_03806_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2601_03806_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

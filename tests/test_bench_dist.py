@@ -57,3 +57,27 @@ def test_single_rank_helpers():
     assert abs(bench.job_mlups(512 ** 3, 50, 5000.0, 1) - 512 ** 3 * 50 / 5.0 / 1e6) < 1e-6
     args = bench.parse_args([])
     assert (args.gpus, args.steps, args.warmup, args.impl, args.size) == (1, 50, 5, "ours", 512)
+
+
+# ---------------------------------------------------------------------------
+# The source hash that ties a traffic record to its kernel
+
+
+def _bench():
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+    return bench
+
+
+def test_strip_comments_keeps_code_and_literals():
+    b = _bench()
+    src = ('int a = 1; // c\n/* x\n y */ char s[] = "a // b \\" /* c */";\n'
+           "char q = '\"';\n\n  // only a comment\nint b;  \n")
+    assert b.strip_comments(src) == ('int a = 1;\n  char s[] = "a // b \\" /* c */";\n'
+                                     "char q = '\"';\nint b;")
+    # a change of code changes the hash input, a change of comment does not
+    assert b.strip_comments("x = 1; // one") == b.strip_comments("x = 1; // uno")
+    assert b.strip_comments("x = 1;") != b.strip_comments("x = 2;")
+
