@@ -817,7 +817,11 @@ def run_learned(args, rank, local, ws):
     value = job_mlups(N, args.steps, max_ms, ws)
     peak, peak_src = measured_hbm_peak()
     achieved = BYTES_PER_NODE["fp32"] * N / (k_ms / 1e3) / 1e9
-    flop_node = 2 * 128 * (32 * 64 + 64 * 64 + 64 * 32) // 128   # padded MMA shapes per node
+    # the network's multiply-adds per node (28-64-64-27); the tensor pipe
+    # executes the padded shapes with the bias columns, K 32 / 80 / 80 and
+    # N 64 / 64 / 32
+    flop_node = 2 * (28 * 64 + 64 * 64 + 64 * 27)
+    flop_node_issued = 2 * (32 * 64 + 80 * 64 + 80 * 32)
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             tpk, tsrc = float(json.load(fh)["bf16_tflops_sustained"]), "of measured (sustained)"
@@ -829,7 +833,8 @@ def run_learned(args, rank, local, ws):
                 "kernel": "flbm::k_step_learned<uint32,*,stats> (GMF + tcgen05 MLP correction)",
                 "kernel_ms": k_ms, "algorithmic_bytes_per_launch": BYTES_PER_NODE["fp32"] * N,
                 "tensor": {"achieved_tflops": tflops, "peak_tflops": tpk, "frac": tflops / tpk,
-                           "peak_source": tsrc, "flop_per_node": flop_node}}
+                           "peak_source": tsrc, "flop_per_node": flop_node,
+                           "issued_flop_per_node": flop_node_issued}}
     u2 = [x / (kT / rho0) for x in st["u2_avg"]]
 
     e2e = None

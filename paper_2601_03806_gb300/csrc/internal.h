@@ -155,9 +155,9 @@ void set_thread_error(const char *msg);
 #include <vector>
 
 namespace flbm {
-// Learned-collision network: the bf16 weight image + FP32 biases in the
-// tensor-core operand layout (mlp_infer.cu) from the flat FP32 parameter
-// vector of include/flbm.h (FLBM_MLP_NPARAM values).
+// Learned-collision network: the bf16 image of weights and split biases in
+// the tensor-core operand layout (mlp_tc.cuh, mlp_infer.cu) from the flat
+// FP32 parameter vector of include/flbm.h (FLBM_MLP_NPARAM values).
 void build_mlp_image(const float *params, std::vector<unsigned char> &img);
 // The learned step (step_learned.cu): GMF collision + network correction.
 struct LearnArgs {

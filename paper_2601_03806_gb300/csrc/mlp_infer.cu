@@ -24,6 +24,27 @@ uint16_t bf16_rne(float f)
     return uint16_t(u >> 16);
 }
 
+float bf16_value(uint16_t h)
+{
+    const uint32_t u = uint32_t(h) << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// b = hi + mid + lo with bf16 parts, each taken to nearest of what is left
+// (8 significant bits a part: together the 24 of an FP32 b), then scaled by
+// s, a power of two (exact).
+void bias_parts(float b, float s, uint16_t (&out)[3])
+{
+    float r = b;
+    for (int k = 0; k < 3; ++k) {
+        const uint16_t h = bf16_rne(r);
+        r -= bf16_value(h);   // exact: the rounding error of a representable r
+        out[k] = bf16_rne(s * bf16_value(h));
+    }
+}
+
 void put(std::vector<unsigned char> &img, uint32_t off, uint16_t v) { std::memcpy(&img[off], &v, 2); }
 
 __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_infer(const float *__restrict__ x, float *__restrict__ y,
@@ -58,19 +79,28 @@ void build_mlp_image(const float *p, std::vector<unsigned char> &img)
 {
     img.assign(kMlpImageBytes, 0);
     const float *W1 = p, *b1 = p + 1792, *W2 = p + 1856, *b2 = p + 5952, *W3 = p + 6016, *b3 = p + 7744;
-    for (uint32_t nrow = 0; nrow < 64; ++nrow)
-        for (uint32_t k = 0; k < 32; ++k)
-            put(img, kW1Off + core_offset(nrow, k, kSbo32), k < 28 ? bf16_rne(W1[nrow * 28 + k]) : 0);
-    for (uint32_t nrow = 0; nrow < 64; ++nrow)
-        for (uint32_t k = 0; k < 64; ++k) put(img, kW2Off + core_offset(nrow, k, kSbo64), bf16_rne(W2[nrow * 64 + k]));
-    for (uint32_t nrow = 0; nrow < 32; ++nrow)
+    // layers 1 and 2 halved (a power of two: exact in bf16), layer 3 as is;
+    // the bias parts go to K columns 28..30 of W1' and 0..2 of B2' / B3
+    for (uint32_t nrow = 0; nrow < 64; ++nrow) {
+        uint16_t bp[3];
+        bias_parts(b1[nrow], 0.5f, bp);
+        for (uint32_t k = 0; k < 32; ++k) {
+            const uint16_t v = k < 28 ? bf16_rne(0.5f * W1[nrow * 28 + k]) : (k < 31 ? bp[k - 28] : 0);
+            put(img, kW1Off + core_offset(nrow, k, kSbo32), v);
+        }
         for (uint32_t k = 0; k < 64; ++k)
-            put(img, kW3Off + core_offset(nrow, k, kSbo64), nrow < 27 ? bf16_rne(W3[nrow * 64 + k]) : 0);
-    float bias[160] = {};
-    for (int i = 0; i < 64; ++i) bias[i] = b1[i];
-    for (int i = 0; i < 64; ++i) bias[64 + i] = b2[i];
-    for (int i = 0; i < 27; ++i) bias[128 + i] = b3[i];
-    std::memcpy(&img[kBiasOff], bias, sizeof(bias));
+            put(img, kW2Off + core_offset(nrow, k, kSbo64), bf16_rne(0.5f * W2[nrow * 64 + k]));
+        bias_parts(b2[nrow], 0.5f, bp);
+        for (uint32_t k = 0; k < 3; ++k) put(img, kB2Off + core_offset(nrow, k, kSbo16), bp[k]);
+    }
+    for (uint32_t nrow = 0; nrow < 27; ++nrow) {
+        for (uint32_t k = 0; k < 64; ++k) put(img, kW3Off + core_offset(nrow, k, kSbo64), bf16_rne(W3[nrow * 64 + k]));
+        uint16_t bp[3];
+        bias_parts(b3[nrow], 1.0f, bp);
+        for (uint32_t k = 0; k < 3; ++k) put(img, kB3Off + core_offset(nrow, k, kSbo16), bp[k]);
+    }
+    for (uint32_t row = 0; row < 128; ++row)
+        for (uint32_t k = 0; k < 3; ++k) put(img, kOnesOff + core_offset(row, k, kSbo16), bf16_rne(1.0f));
 }
 
 }  // namespace flbm

@@ -7,13 +7,18 @@
 // row t % 128 of sub-tile t / 128 (warp w reads tensor-memory lanes
 // 32 (w % 4) .. + 31, its rows), and sub-tile q owns tensor-memory columns
 // 128 q .. 128 q + 127 (all 512 columns of the SM).  Per sub-tile
-//   A1[128 x 32]  bf16 features (28 + 4 zero columns)      -> shared memory
-//   D1 = A1 W1^T  (M 128, N 64, K 32: two MMAs)             -> tensor memory cols 0..63
-//   h1 = silu(D1 + b1) as bf16                               -> A2 (shared)
-//   D2 = h1 W2^T  (N 64, K 64: four MMAs)                    -> cols 64..127
-//   h2 = silu(D2 + b2) as bf16                               -> A2 again
-//   D3 = h2 W3^T  (N 32, K 64: four MMAs; rows 27..31 of W3 are zero) -> cols 0..31
-//   y = D3 + b3                                              -> thread t's registers
+//   A1[128 x 32]  bf16 features, then 1, 1, 1, 0            -> shared memory
+//   D1 = A1 W1'^T (M 128, N 64, K 32: two MMAs)             -> tensor memory cols 0..63
+//   h1 = silu(z1) = hz (1 + tanh hz), hz = D1, as bf16       -> A2 (shared)
+//   D2 = [h1 | U] W2'^T  (N 64, K 64 + 16: five MMAs)        -> cols 64..127
+//   h2 = silu(z2), hz = D2, as bf16                          -> A2 again
+//   y  = [h2 | U] W3'^T  (N 32, K 64 + 16: five MMAs; rows 27..31 zero) -> cols 0..31
+// The biases ride in the MMAs: each is split into three bf16 parts
+// b = b_hi + b_mid + b_lo (exact to FP32) that multiply constant-one
+// columns -- A1's padding columns 28..30 for layer 1, the shared block U
+// (128 x 16, columns 0..2 one) for layers 2 and 3 -- and W1, b1, W2, b2 are
+// stored halved (exact in bf16), so the accumulators hold z / 2 and SiLU
+// costs one tanh and one FMA per activation.
 // Each sub-tile is an independent group of 4 warps (128 threads) with its
 // own named barrier (id 1 + group), its own mbarrier and its own MMA issuer,
 // so the groups drift out of phase and one group's epilogue fills another's
@@ -31,17 +36,19 @@
 namespace flbm {
 
 constexpr int kMlpIn = 28, kMlpHidden = 64, kMlpOut = 27;
+constexpr uint32_t kSbo16 = 2 * 128;          // SBO of a K = 16 operand
 constexpr uint32_t kSbo32 = 4 * 128;          // SBO of a K = 32 operand
 constexpr uint32_t kSbo64 = 8 * 128;          // SBO of a K = 64 operand
-constexpr uint32_t kW1Off = 0, kW2Off = 4096, kW3Off = 12288, kBiasOff = 16384;
-constexpr uint32_t kMlpImageBytes = kBiasOff + (64 + 64 + 32) * 4;   // 17,024 B
+// image: W1' [64 x 32] | W2' [64 x 64] | W3 [32 x 64] | B2' [64 x 16] |
+// B3 [32 x 16] | U [128 x 16], all bf16 in the operand layout of umma.cuh
+constexpr uint32_t kW1Off = 0, kW2Off = 4096, kW3Off = 12288, kB2Off = 16384, kB3Off = 18432, kOnesOff = 19456;
+constexpr uint32_t kMlpImageBytes = kOnesOff + 128 * 16 * 2;   // 23,552 B
 constexpr uint32_t kMlpSub = 4;                 // sub-tiles of 128 rows per CTA
 constexpr uint32_t kMlpThreads = 128 * kMlpSub;  // CTA size
 constexpr uint32_t kMlpTmemCols = 128 * kMlpSub; // the whole tensor memory of an SM
 
 struct MlpSmem {
-    __align__(128) unsigned char w[kBiasOff];          // W1 | W2 | W3 bf16 images
-    float bias[64 + 64 + 32];                          // b1 | b2 | b3 (b3 zero-padded)
+    __align__(128) unsigned char w[kMlpImageBytes];    // the network image
     __align__(128) unsigned char a1[kMlpSub][128 * 32 * 2];
     __align__(128) unsigned char a2[kMlpSub][128 * 64 * 2];
     uint64_t bar[kMlpSub];
@@ -49,13 +56,13 @@ struct MlpSmem {
 };
 constexpr size_t kMlpSmemBytes = (sizeof(MlpSmem) + 1023) / 1024 * 1024;
 
-// silu(z) = z sigmoid(z) = 0.5 z (1 + tanh(z / 2)), with the hardware tanh
-// (absolute error about 2^-11, below the bf16 rounding of the activations).
-__device__ __forceinline__ float silu_fast(float z)
+// silu(z) = z sigmoid(z) = hz (1 + tanh(hz)) with hz = z / 2, from hz, with
+// the hardware tanh (absolute error about 2^-11, below the bf16 rounding of
+// the activations).
+__device__ __forceinline__ float silu_half(float hz)
 {
     float t;
-    asm("tanh.approx.f32 %0, %1;\n" : "=f"(t) : "f"(0.5f * z));
-    const float hz = 0.5f * z;
+    asm("tanh.approx.f32 %0, %1;\n" : "=f"(t) : "f"(hz));
     return __fmaf_rn(hz, t, hz);
 }
 
@@ -80,14 +87,12 @@ __device__ __forceinline__ void store_row16(unsigned char *base, uint32_t sbo, u
     }
 }
 
-// CTA set-up: weight image to shared memory, mbarrier, tensor memory.
+// CTA set-up: network image to shared memory, mbarriers, tensor memory.
 __device__ __forceinline__ void mlp_setup(MlpSmem &sm, const unsigned char *__restrict__ img)
 {
     const uint4 *src = reinterpret_cast<const uint4 *>(img);
     uint4 *dst = reinterpret_cast<uint4 *>(sm.w);
-    for (uint32_t i = threadIdx.x; i < kBiasOff / 16; i += blockDim.x) dst[i] = src[i];
-    const float *bsrc = reinterpret_cast<const float *>(img + kBiasOff);
-    for (uint32_t i = threadIdx.x; i < 160; i += blockDim.x) sm.bias[i] = bsrc[i];
+    for (uint32_t i = threadIdx.x; i < kMlpImageBytes / 16; i += blockDim.x) dst[i] = src[i];
     if (threadIdx.x == 0) {
         for (uint32_t q = 0; q < kMlpSub; ++q) mbar_init(&sm.bar[q], 1);
         mbar_init_fence();
@@ -165,7 +170,7 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
         for (int i = 0; i < 16; ++i) v[i] = x[i];
         store_row16(a1p, kSbo32, t, 0, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = (16 + i < kMlpIn) ? x[16 + i] : 0.0f;
+        for (int i = 0; i < 16; ++i) v[i] = (16 + i < kMlpIn) ? x[16 + i] : (16 + i < kMlpIn + 3 ? 1.0f : 0.0f);
         store_row16(a1p, kSbo32, t, 16, v);
     }
     mlp_sync_for_mma(q);
@@ -186,7 +191,7 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
             float z[16];
             tmem_ld16(tmem + lane_base + 16 * ch, z);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) z[i] = silu_fast(z[i] + sm.bias[16 * ch + i]);
+            for (int i = 0; i < 16; ++i) z[i] = silu_half(z[i]);
             store_row16(a2p, kSbo64, t, 16 * ch, z);
         }
         mlp_sync_for_mma(q);
@@ -197,6 +202,8 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
             for (uint32_t s = 0; s < 4; ++s)
                 umma_bf16(tmem + 64, umma_smem_desc(a2 + 256 * s, 128, kSbo64),
                           umma_smem_desc(w + kW2Off + 256 * s, 128, kSbo64), idesc64, s > 0);
+            umma_bf16(tmem + 64, umma_smem_desc(w + kOnesOff, 128, kSbo16),
+                      umma_smem_desc(w + kB2Off, 128, kSbo16), idesc64, true);
             umma_commit(&sm.bar[q]);
         }
         ok = mlp_wait(sm, q, phase);
@@ -207,7 +214,7 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
             float z[16];
             tmem_ld16(tmem + lane_base + 64 + 16 * ch, z);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) z[i] = silu_fast(z[i] + sm.bias[64 + 16 * ch + i]);
+            for (int i = 0; i < 16; ++i) z[i] = silu_half(z[i]);
             store_row16(a2p, kSbo64, t, 16 * ch, z);
         }
         mlp_sync_for_mma(q);
@@ -218,6 +225,8 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
             for (uint32_t s = 0; s < 4; ++s)
                 umma_bf16(tmem, umma_smem_desc(a2 + 256 * s, 128, kSbo64),
                           umma_smem_desc(w + kW3Off + 256 * s, 128, kSbo64), idesc32, s > 0);
+            umma_bf16(tmem, umma_smem_desc(w + kOnesOff, 128, kSbo16),
+                      umma_smem_desc(w + kB3Off, 128, kSbo16), idesc32, true);
             umma_commit(&sm.bar[q]);
         }
         ok = mlp_wait(sm, q, phase);
@@ -229,7 +238,7 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
             tmem_ld16(tmem + lane_base + 16 * ch, z);
 #pragma unroll
             for (int i = 0; i < 16; ++i)
-                if (16 * ch + i < kMlpOut) y[16 * ch + i] = z[i] + sm.bias[128 + 16 * ch + i];
+                if (16 * ch + i < kMlpOut) y[16 * ch + i] = z[i];
         }
         return true;
     }
