@@ -4,14 +4,21 @@
 // A CTA of 512 threads (one per SM: it allocates tensor memory) takes four
 // row chunks of 128 consecutive x-nodes (the chunking of the direct step
 // kernel) at a time, one per network sub-tile; threads past a row end or
-// past the last chunk only take part in the tile.  Each thread loads its
-// node's 27 incoming
-// populations (AA pattern), writes the node's features to the network tile,
-// and, while the first layer's tensor-core MMAs run, collides the node with
-// the GMF collision (collide_core, noise included).  Then it adds
+// past the last chunk only take part in the tile.  Each thread's node's 27
+// incoming populations (AA pattern) arrive in its own column of a shared
+// staging buffer by 4-byte cp.async, issued one round ahead, so the global
+// latency hides behind the previous node's work; no other thread touches
+// that column, so the thread's own wait suffices.  The thread writes the
+// node's features to the network tile, and, while the first layer's
+// tensor-core MMAs run, starts the next round's copies and collides the node
+// with the GMF collision (collide_core, noise included).  Then it adds
 // P(w_i sigma^3 y_i), the network output mapped to populations with mass and
 // momentum projected out, and stores (AA pattern).  The network runs on the
 // tcgen05 path of mlp_tc.cuh.
+//
+// Early reads are safe in place: under the AA pattern the locations a node
+// reads are exactly those it writes, so no other node's store can land on a
+// staged value.
 #include "../../include/flbm.h"
 #include "internal.h"
 #include "mlp_tc.cuh"
@@ -20,31 +27,83 @@ namespace flbm {
 
 namespace {
 
+constexpr size_t kStageBytes = size_t(kQ) * kMlpThreads * sizeof(float);   // [27][512] floats
+constexpr size_t kLearnSmemBytes = kMlpSmemBytes + kStageBytes;
+
+// This thread's node in super-chunk sc (x = 0 when inactive).
+struct Site {
+    uint32_t x, y, z;
+    bool active;
+};
+__device__ __forceinline__ Site locate(const StepArgs<float> &a, uint64_t sc)
+{
+    const uint64_t ch0 = sc * kMlpSub + (threadIdx.x >> 7);
+    const bool live = ch0 < a.nchunks;
+    const uint64_t ch = live ? ch0 : 0;
+    const uint32_t xc = uint32_t(ch % a.cpr);
+    const uint64_t r = ch / a.cpr;
+    Site s;
+    s.y = uint32_t(r % a.ny);
+    s.z = uint32_t(r / a.ny);
+    s.x = xc * 128 + (threadIdx.x & 127u);
+    s.active = live && s.x < a.nx;
+    if (!s.active) s.x = 0;
+    return s;
+}
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Population c = (i-1, j-1, k-1) of node (x, y, z) as the AA pattern reads it.
+template <typename I, bool ODD>
+__device__ __forceinline__ I load_index(const Nbr<I> &nb, I N, int i, int j, int k)
+{
+    if (!ODD) return I(slot_of(i - 1, j - 1, k - 1)) * N + nb.node();
+    return I(slot_of(1 - i, 1 - j, 1 - k)) * N + (nb.xs[2 - i] + nb.ry[2 - j] + nb.rz[2 - k]);
+}
+
+// Start the copies of this thread's node of super-chunk sc into its column.
+template <typename I, bool ODD>
+__device__ __forceinline__ void stage_node(const float *g, float *stage, const StepArgs<float> &a, uint64_t sc)
+{
+    const Site s = locate(a, sc);
+    if (s.active) {
+        const Nbr<I> nb(s.x, s.y, s.z, a.nx, a.ny, a.nz);
+        const I N = I(a.n);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    cp_async4(stage + (9 * i + 3 * j + k) * kMlpThreads + threadIdx.x,
+                              g + load_index<I, ODD>(nb, N, i, j, k));
+    }
+    cp_async_commit();
+}
+
 template <typename I, bool ODD, bool STATS>
 __global__ void __launch_bounds__(kMlpThreads, 1) k_step_learned(float *__restrict__ g, const StepArgs<float> a,
                                                          const LearnArgs L)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
     MlpSmem &sm = *reinterpret_cast<MlpSmem *>(smraw);
+    float *stage = reinterpret_cast<float *>(smraw + kMlpSmemBytes);
+    const uint64_t nsuper = (a.nchunks + kMlpSub - 1) / kMlpSub;
+    if (blockIdx.x < nsuper) stage_node<I, ODD>(g, stage, a, blockIdx.x);
     mlp_setup(sm, L.img);
     uint32_t phase = 0;
     float acc[NSTAT];
 #pragma unroll
     for (int s = 0; s < NSTAT; ++s) acc[s] = 0.0f;
     const I N = I(a.n);
-    const uint64_t nsuper = (a.nchunks + kMlpSub - 1) / kMlpSub;
     for (uint64_t sc = blockIdx.x; sc < nsuper; sc += gridDim.x) {
-        const uint64_t ch0 = sc * kMlpSub + (threadIdx.x >> 7);
-        const bool live = ch0 < a.nchunks;
-        const uint64_t ch = live ? ch0 : 0;
-        const uint32_t xc = uint32_t(ch % a.cpr);
-        const uint64_t r = ch / a.cpr;
-        const uint32_t y = uint32_t(r % a.ny);
-        const uint32_t z = uint32_t(r / a.ny);
-        const uint32_t x = xc * 128 + (threadIdx.x & 127u);
-        const bool active = live && x < a.nx;
-        const Nbr<I> nb(active ? x : 0, y, z, a.nx, a.ny, a.nz);
-        const I n = nb.node();
+        const Site cur = locate(a, sc);
+        cp_async_wait_all();
         float v[3][3][3];
         float xf[kMlpIn];
 #pragma unroll
@@ -53,24 +112,28 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_step_learned(float *__restri
             for (int j = 0; j < 3; ++j)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    I idx;
-                    if (!ODD) idx = I(slot_of(i - 1, j - 1, k - 1)) * N + n;
-                    else idx = I(slot_of(1 - i, 1 - j, 1 - k)) * N + (nb.xs[2 - i] + nb.ry[2 - j] + nb.rz[2 - k]);
-                    v[i][j][k] = active ? __ldcg(g + idx) : 0.0f;
+                    v[i][j][k] = cur.active ? stage[(9 * i + 3 * j + k) * kMlpThreads + threadIdx.x] : 0.0f;
                     // feature of population c = (i-1, j-1, k-1): g_c / sqrt(rho0 kT w_c / c_s^2)
                     xf[slot_of(i - 1, j - 1, k - 1)] = v[i][j][k] * L.inv_s[(i != 1) + (j != 1) + (k != 1)];
                 }
-        xf[27] = active ? L.x27 : 0.0f;
+        xf[27] = cur.active ? L.x27 : 0.0f;
         float yv[kMlpOut];
         float nzd[kNoise];   // unused: the collision draws its normals inside
+        const uint64_t next = sc + gridDim.x;
         const bool ok = mlp_tile(sm, phase, xf, yv, [&] {
-            if (active) collide_core<float, 1, STATS, false>(v, a, nzd, uint32_t(n), acc);
+            if (next < nsuper) stage_node<I, ODD>(g, stage, a, next);
+            if (cur.active) {
+                const Nbr<I> nb(cur.x, cur.y, cur.z, a.nx, a.ny, a.nz);
+                collide_core<float, 1, STATS, false>(v, a, nzd, uint32_t(nb.node()), acc);
+            }
         }, L.starve != 0);
         if (!ok) {
             if ((threadIdx.x & 127u) == 0) atomicOr(a.flag, 2u);   // one report per group
             break;
         }
-        if (!active) continue;
+        if (!cur.active) continue;
+        const Nbr<I> nb(cur.x, cur.y, cur.z, a.nx, a.ny, a.nz);
+        const I n = nb.node();
         // correction d_c = w_c sigma^3 y_c, minus its mass and momentum
         float d[3][3][3];
         float alpha = 0.0f, bx = 0.0f, by = 0.0f, bz = 0.0f;
@@ -110,6 +173,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_step_learned(float *__restri
                     __stcs(g + idx, v[i][j][k]);
                 }
     }
+    cp_async_wait_all();   // no copy may land after the CTA has left
     mlp_teardown(sm);
     if (STATS) block_reduce_store(acc, a.partials + size_t(blockIdx.x) * NSTAT);
 }
@@ -119,11 +183,11 @@ cudaError_t launch_t(float *g, const StepArgs<float> &a, const LearnArgs &L, boo
                      cudaStream_t s)
 {
     if (odd) {
-        if (stats) k_step_learned<I, true, true><<<grid, kMlpThreads, kMlpSmemBytes, s>>>(g, a, L);
-        else k_step_learned<I, true, false><<<grid, kMlpThreads, kMlpSmemBytes, s>>>(g, a, L);
+        if (stats) k_step_learned<I, true, true><<<grid, kMlpThreads, kLearnSmemBytes, s>>>(g, a, L);
+        else k_step_learned<I, true, false><<<grid, kMlpThreads, kLearnSmemBytes, s>>>(g, a, L);
     } else {
-        if (stats) k_step_learned<I, false, true><<<grid, kMlpThreads, kMlpSmemBytes, s>>>(g, a, L);
-        else k_step_learned<I, false, false><<<grid, kMlpThreads, kMlpSmemBytes, s>>>(g, a, L);
+        if (stats) k_step_learned<I, false, true><<<grid, kMlpThreads, kLearnSmemBytes, s>>>(g, a, L);
+        else k_step_learned<I, false, false><<<grid, kMlpThreads, kLearnSmemBytes, s>>>(g, a, L);
     }
     return cudaGetLastError();
 }
@@ -142,7 +206,7 @@ cudaError_t launch_step_learned(float *g, const StepArgs<float> &a, const LearnA
 int learned_occupancy(uint64_t n)
 {
     // the sub-tile buffers exceed the 48 KB default
-    const int sm = int(kMlpSmemBytes);
+    const int sm = int(kLearnSmemBytes);
     cudaFuncSetAttribute(k_step_learned<uint32_t, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_step_learned<uint32_t, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_step_learned<uint32_t, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -154,9 +218,9 @@ int learned_occupancy(uint64_t n)
     int nb = 0;
     const cudaError_t e = fits32(n)
         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_learned<uint32_t, true, true>, kMlpThreads,
-                                                        kMlpSmemBytes)
+                                                        kLearnSmemBytes)
         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_learned<uint64_t, true, true>, kMlpThreads,
-                                                        kMlpSmemBytes);
+                                                        kLearnSmemBytes);
     (void)nb;
     (void)e;
     return 1;   // a CTA holds all 512 tensor-memory columns of its SM
