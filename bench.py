@@ -40,6 +40,9 @@ KERNEL_SOURCES = ["step_kernel.cuh", "lattice.cuh", "internal.h", "step_f32.cu"]
 ENS_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_ens_f32_gmf_traffic.txt")
 ENS_KERNEL_SOURCES = ["ens_kernel.cuh", "step_kernel.cuh", "lattice.cuh", "internal.h", "stats.cuh",
                       "ens_f32.cu"]
+LEARNED_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_learned_f32_traffic.txt")
+LEARNED_KERNEL_SOURCES = ["step_learned.cu", "mlp_tc.cuh", "umma.cuh", "step_kernel.cuh", "lattice.cuh",
+                          "internal.h"]
 
 
 def parse_args(argv=None):
@@ -829,7 +832,8 @@ def run_learned(args, rank, local, ws):
         tpk, tsrc = 1700.0, "of fallback"
     tflops = flop_node * N / (k_ms / 1e3) / 1e12
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_src, "traffic": None,
+                "peak_source": peak_src,
+                "traffic": recorded_traffic(N, LEARNED_TRAFFIC_FILE, LEARNED_KERNEL_SOURCES),
                 "kernel": "flbm::k_step_learned<uint32,*,stats> (GMF + tcgen05 MLP correction)",
                 "kernel_ms": k_ms, "algorithmic_bytes_per_launch": BYTES_PER_NODE["fp32"] * N,
                 "tensor": {"achieved_tflops": tflops, "peak_tflops": tpk, "frac": tflops / tpk,

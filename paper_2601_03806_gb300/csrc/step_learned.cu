@@ -30,24 +30,48 @@ namespace {
 constexpr size_t kStageBytes = size_t(kQ) * kMlpThreads * sizeof(float);   // [27][512] floats
 constexpr size_t kLearnSmemBytes = kMlpSmemBytes + kStageBytes;
 
-// This thread's node in super-chunk sc (x = 0 when inactive).
+// Position (x-chunk, y, z) of this thread's row chunk; chunk ch = (z ny + y)
+// cpr + xc.  Across the rounds a thread's chunk advances by 4 x gridDim.x,
+// decomposed once in the same mixed radix, so a round costs two carries
+// instead of two divisions.
+struct Walk {
+    uint32_t xc, y, z;
+};
+__device__ __forceinline__ Walk walk_of(const StepArgs<float> &a, uint64_t ch)
+{
+    const uint64_t r = ch / a.cpr;
+    return Walk{uint32_t(ch % a.cpr), uint32_t(r % a.ny), uint32_t(r / a.ny)};
+}
+__device__ __forceinline__ Walk advance(Walk w, const Walk &d, const StepArgs<float> &a)
+{
+    w.xc += d.xc;
+    w.y += d.y;
+    w.z += d.z;
+    if (w.xc >= a.cpr) {
+        w.xc -= a.cpr;
+        ++w.y;
+    }
+    if (w.y >= a.ny) {
+        w.y -= a.ny;
+        ++w.z;
+    }
+    return w;
+}
+
+// This thread's node at walk position w (x = 0 when inactive: past a row's
+// end, or z past the box for chunks beyond the last).
 struct Site {
     uint32_t x, y, z;
     bool active;
 };
-__device__ __forceinline__ Site locate(const StepArgs<float> &a, uint64_t sc)
+__device__ __forceinline__ Site site_of(const Walk &w, const StepArgs<float> &a)
 {
-    const uint64_t ch0 = sc * kMlpSub + (threadIdx.x >> 7);
-    const bool live = ch0 < a.nchunks;
-    const uint64_t ch = live ? ch0 : 0;
-    const uint32_t xc = uint32_t(ch % a.cpr);
-    const uint64_t r = ch / a.cpr;
     Site s;
-    s.y = uint32_t(r % a.ny);
-    s.z = uint32_t(r / a.ny);
-    s.x = xc * 128 + (threadIdx.x & 127u);
-    s.active = live && s.x < a.nx;
-    if (!s.active) s.x = 0;
+    s.x = w.xc * 128 + (threadIdx.x & 127u);
+    s.y = w.y;
+    s.z = w.z;
+    s.active = w.z < a.nz && s.x < a.nx;
+    if (!s.active) s.x = s.y = s.z = 0;
     return s;
 }
 
@@ -66,11 +90,10 @@ __device__ __forceinline__ I load_index(const Nbr<I> &nb, I N, int i, int j, int
     return I(slot_of(1 - i, 1 - j, 1 - k)) * N + (nb.xs[2 - i] + nb.ry[2 - j] + nb.rz[2 - k]);
 }
 
-// Start the copies of this thread's node of super-chunk sc into its column.
+// Start the copies of this thread's node at site s into its column.
 template <typename I, bool ODD>
-__device__ __forceinline__ void stage_node(const float *g, float *stage, const StepArgs<float> &a, uint64_t sc)
+__device__ __forceinline__ void stage_node(const float *g, float *stage, const StepArgs<float> &a, const Site &s)
 {
-    const Site s = locate(a, sc);
     if (s.active) {
         const Nbr<I> nb(s.x, s.y, s.z, a.nx, a.ny, a.nz);
         const I N = I(a.n);
@@ -94,7 +117,9 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_step_learned(float *__restri
     MlpSmem &sm = *reinterpret_cast<MlpSmem *>(smraw);
     float *stage = reinterpret_cast<float *>(smraw + kMlpSmemBytes);
     const uint64_t nsuper = (a.nchunks + kMlpSub - 1) / kMlpSub;
-    if (blockIdx.x < nsuper) stage_node<I, ODD>(g, stage, a, blockIdx.x);
+    Walk w = walk_of(a, uint64_t(blockIdx.x) * kMlpSub + (threadIdx.x >> 7));
+    const Walk step = walk_of(a, uint64_t(gridDim.x) * kMlpSub);
+    if (blockIdx.x < nsuper) stage_node<I, ODD>(g, stage, a, site_of(w, a));
     mlp_setup(sm, L.img);
     uint32_t phase = 0;
     float acc[NSTAT];
@@ -102,7 +127,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_step_learned(float *__restri
     for (int s = 0; s < NSTAT; ++s) acc[s] = 0.0f;
     const I N = I(a.n);
     for (uint64_t sc = blockIdx.x; sc < nsuper; sc += gridDim.x) {
-        const Site cur = locate(a, sc);
+        const Site cur = site_of(w, a);
+        w = advance(w, step, a);
         cp_async_wait_all();
         float v[3][3][3];
         float xf[kMlpIn];
@@ -121,7 +147,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_step_learned(float *__restri
         float nzd[kNoise];   // unused: the collision draws its normals inside
         const uint64_t next = sc + gridDim.x;
         const bool ok = mlp_tile(sm, phase, xf, yv, [&] {
-            if (next < nsuper) stage_node<I, ODD>(g, stage, a, next);
+            if (next < nsuper) stage_node<I, ODD>(g, stage, a, site_of(w, a));
             if (cur.active) {
                 const Nbr<I> nb(cur.x, cur.y, cur.z, a.nx, a.ny, a.nz);
                 collide_core<float, 1, STATS, false>(v, a, nzd, uint32_t(nb.node()), acc);
