@@ -41,6 +41,9 @@ ENS_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_ens_f32_gmf_traffic.tx
 ENS_KERNEL_SOURCES = ["ens_kernel.cuh", "step_kernel.cuh", "lattice.cuh", "internal.h", "stats.cuh",
                       "ens_f32.cu"]
 LEARNED_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_learned_f32_traffic.txt")
+MS_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_ms_step_f32_gmf_traffic.txt")
+MS_KERNEL_SOURCES = ["mstate.cu", "step_kernel.cuh", "lattice.cuh", "internal.h"]
+MS_BYTES_PER_NODE = 10 * 4 * 2   # moment state: ten FP32 numbers read and written per node
 LEARNED_KERNEL_SOURCES = ["step_learned.cu", "mlp_tc.cuh", "umma.cuh", "step_kernel.cuh", "lattice.cuh",
                           "internal.h"]
 
@@ -56,6 +59,9 @@ def parse_args(argv=None):
                     help="non-cubic box (profiling runs); overrides --size")
     ap.add_argument("--precision", choices=["fp32", "fp16", "fp64"], default="fp32",
                     help="population storage (fp32 = the benchmark workload)")
+    ap.add_argument("--state-form", choices=["populations", "moments"], default="populations",
+                    help="box: what the box keeps between steps (moments: the thread-safe form, "
+                         "ten FP32 numbers per node, FP32 GMF only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", choices=["box", "ensemble", "learned"], default="box",
@@ -362,10 +368,21 @@ def metric_name():
     return "MLUPS of the fused GMF-FLBM D3Q27 stream-and-collide step (HBM roofline fraction beside it)"
 
 
-def workload_config(size, ws, precision="fp32", box=None):
+def workload_config(size, ws, precision="fp32", box=None, moments=False):
     es = BYTES_PER_NODE[precision] // 54
     nx, ny, nz = box if box else (size, size, size)
     shape = "%d^3" % size if nx == ny == nz else "%dx%dx%d" % (nx, ny, nz)
+    if moments:
+        return {"workload": "GMF-FLBM D3Q27 periodic %s in the moment-state (thread-safe) form: ten "
+                            "FP32 numbers per node between steps, populations rebuilt from the "
+                            "neighbours' numbers and regenerated noise; rho0=1, kT=1e-5, tau=0.6, "
+                            "FP64 reductions every step" % shape,
+                "nx": nx, "ny": ny, "nz": nz, "tau": WORKLOAD["tau"], "kT": WORKLOAD["kT"],
+                "rho0": WORKLOAD["rho0"], "scheme": "gmf",
+                "storage": "moment state, 2 x 10 FP32 arrays (ping-pong)",
+                "stats_every": 1, "l2": "inputs larger than L2 (%.1f GB state vs 129 MB L2)"
+                % (40 * nx * ny * nz / 1e9),
+                "parallelism": "replicas x%d (one independent box per GPU)" % ws}
     return {"workload": "GMF-FLBM D3Q27 periodic %s, %s deviation populations AA in place, "
                         "rho0=1, kT=1e-5, tau=0.6, FP64 reductions every step"
                         % (shape, precision.upper()),
@@ -394,8 +411,12 @@ def run_ours(args, rank, local, ws):
     stream = torch.cuda.Stream(device=dev)
     prec = {"fp32": flbm.FLBM_FP32, "fp16": flbm.FLBM_FP16, "fp64": flbm.FLBM_FP64}[args.precision]
     es = BYTES_PER_NODE[args.precision] // 54
+    moments = args.state_form == "moments"
+    if moments and args.precision != "fp32":
+        raise SystemExit("--state-form moments runs on FP32 storage")
     lat = flbm.Lattice(nx, ny, nz, tau, kT, rho0=rho0, seed=seed, precision=prec,
-                       stats_every=1, torch_memory=True, stream=stream)
+                       stats_every=1, torch_memory=True, stream=stream,
+                       state_form=flbm.FLBM_STATE_MOMENTS if moments else flbm.FLBM_STATE_POPULATIONS)
     lat.init_thermal(seed)           # invariant-measure start (library kernel)
     lat.step(args.warmup)
     lat.stats_reset()
@@ -423,7 +444,8 @@ def run_ours(args, rank, local, ws):
 
     k_ms = kernel_ms / max(launches, 1)
     peak, peak_src = measured_hbm_peak()
-    achieved = BYTES_PER_NODE[args.precision] * N / (k_ms / 1e3) / 1e9
+    node_bytes = MS_BYTES_PER_NODE if moments else BYTES_PER_NODE[args.precision]
+    achieved = node_bytes * N / (k_ms / 1e3) / 1e9
     traffic = recorded_traffic(N) if args.precision == "fp32" else None
     rows_path = nx % 32 == 0 and 2 * 27 * nx * es <= 200 * 1024 and os.environ.get("FLBM_ROWS", "1") != "0"
     st_name = {"fp32": "float", "fp16": "__half", "fp64": "double"}[args.precision]
@@ -431,10 +453,13 @@ def run_ours(args, rank, local, ws):
              else "flbm::k_step<%s,GMF,*,stats> (direct)" % st_name)
     if not rows_path:
         traffic = None
+    if moments:
+        kname = "flbm::k_ms_step<GMF,stats> (moment state, z-marching columns)"
+        traffic = recorded_traffic(N, MS_TRAFFIC_FILE, MS_KERNEL_SOURCES)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
                 "traffic": traffic, "kernel": kname,
-                "kernel_ms": k_ms, "algorithmic_bytes_per_launch": BYTES_PER_NODE[args.precision] * N}
+                "kernel_ms": k_ms, "algorithmic_bytes_per_launch": node_bytes * N}
 
     u2_ratio = [x / (kT / rho0) for x in st["u2_avg"]]
 
@@ -498,7 +523,7 @@ def run_ours(args, rank, local, ws):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "fp16": "f16 storage / f32 arithmetic", "fp64": "f64"}[args.precision],
-            "data": "synthetic", "config": workload_config(n, ws, args.precision, (nx, ny, nz)),
+            "data": "synthetic", "config": workload_config(n, ws, args.precision, (nx, ny, nz), moments),
             "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches) + int(args.steps),

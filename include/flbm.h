@@ -59,6 +59,21 @@ typedef struct flbm_ctx flbm_ctx; /* opaque, owned by the library */
  * network set with flbm_set_mlp before the first step. */
 enum flbm_scheme { FLBM_BGK = 0, FLBM_GMF = 1, FLBM_REG = 2, FLBM_LEARNED = 3 };
 
+/* What a box keeps between steps (flbm_params.state_form).
+ * POPULATIONS: the 27 populations, in place with the AA pattern (216 B of
+ *   traffic per node and step in FP32).
+ * MOMENTS: the paper's thread-safe formulation (end of Sec. II): per node
+ *   the ten deterministic numbers of its last collision, rho - rho0, j and
+ *   the relaxed second-order amplitudes, in two library-owned arrays of
+ *   10 N floats; each step rebuilds the populations a node pulls from its
+ *   neighbours' numbers and their regenerated noise (80 B of state traffic
+ *   per node and step).  FP32, GMF or Reg only (BGK's ghost modes keep a
+ *   memory of their own).  The results are those of the population form, bit
+ *   for bit.  The population buffer stays: the first step after the
+ *   populations were written collides from it, and any call that reads
+ *   populations rebuilds them into it first. */
+enum flbm_state_form { FLBM_STATE_POPULATIONS = 0, FLBM_STATE_MOMENTS = 1 };
+
 /* Storage precision of the populations.
  * FLBM_FP64: deviations g_i = f_i - w_i rho0 in double, FP64 arithmetic.
  * FLBM_FP32: deviations in float, FP32 arithmetic (FP64 only for the global
@@ -101,6 +116,7 @@ typedef struct flbm_params {
                               counter word 2 is block | s << 8, so boxes under
                               one seed with distinct streams draw independent
                               noise (0: the default stream) */
+    int32_t state_form;    /* flbm_state_form (0: populations) */
     double tau;            /* relaxation time, > 0.5 (omega = 1/tau) */
     double kT;             /* thermal energy k_B T >= 0 (lattice units) */
     double rho0;           /* reference density > 0; initial state f_i = w_i rho0 */

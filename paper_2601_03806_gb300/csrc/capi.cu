@@ -103,6 +103,11 @@ std::string flbm::validate_params(const flbm_params *p)
     if (p->stats_every < 0) return "stats_every must be >= 0";
     if (p->noise_rho0 != 0 && p->noise_rho0 != 1) return "noise_rho0 must be 0 or 1";
     if (p->noise_stream < 0 || p->noise_stream >= (1 << 24)) return "noise_stream must be in [0, 2^24)";
+    if (p->state_form != FLBM_STATE_POPULATIONS && p->state_form != FLBM_STATE_MOMENTS)
+        return "unknown state_form";
+    if (p->state_form == FLBM_STATE_MOMENTS &&
+        (p->precision != FLBM_FP32 || (p->scheme != FLBM_GMF && p->scheme != FLBM_REG)))
+        return "the moment-state form runs GMF or Reg on FP32 storage";
     return "";
 }
 
@@ -201,6 +206,25 @@ int ensure_pipe(flbm_ctx *c)
 // Device -> host in chunks of pipe_nodes: produce(buf, n0, cn) fills a
 // staging buffer on the context stream, copy(buf, n0, cn) drains it on the
 // copy stream; chunk k + 1 is produced while chunk k is copied.
+// Moment-state form: rebuild the populations of the current step into the
+// population storage (natural AA form) unless they are current already.
+int materialise(flbm_ctx *c)
+{
+    if (c->pops_valid) return FLBM_OK;
+    CK(c, launch_ms_export(c->ms[c->ms_cur], static_cast<float *>(c->g), make_args<float>(c, c->step - 1),
+                           c->p.scheme, c->ms_grid, c->ms_zseg, c->stream));
+    c->phase = int(c->step & 1);
+    c->pops_valid = true;
+    return FLBM_OK;
+}
+
+// The populations were replaced: the next step collides from them.
+void populations_written(flbm_ctx *c)
+{
+    c->ms_live = false;
+    c->pops_valid = true;
+}
+
 template <typename Produce, typename Copy>
 int d2h_chunks(flbm_ctx *c, Produce produce, Copy copy)
 {
@@ -269,6 +293,8 @@ void flbm::destroy_ctx(flbm_ctx *c)
     cudaFree(c->dflags);
     if (c->own_g) cudaFree(c->g);
     cudaFree(c->mlp_img);
+    cudaFree(c->ms[0]);
+    cudaFree(c->ms[1]);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -357,7 +383,18 @@ int flbm::create_ctx(const flbm_params *p, void *dev_buf, size_t dev_bytes, void
         const uint64_t nrows = uint64_t(p->ny) * p->nz;
         c->row_grid = int(std::min<uint64_t>(nrows, uint64_t(c->nsm) * occ_rows));
     }
-    const int max_grid = std::max(c->grid, c->row_grid);
+    if (p->state_form == FLBM_STATE_MOMENTS) {
+        for (int b = 0; b < 2; ++b) {
+            e = cudaMalloc(&c->ms[b], size_t(kMsVals) * c->n * sizeof(float));
+            if (e != cudaSuccess) {
+                c->err = std::string("cudaMalloc(moment state): ") + cudaGetErrorString(e);
+                return bail(FLBM_E_NOMEM);
+            }
+        }
+        e = ms_prepare(p->scheme, c->nsm, make_args<float>(c, 0), c->ms_grid, c->ms_zseg);
+        if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return bail(FLBM_E_CUDA); }
+    }
+    const int max_grid = std::max(std::max(c->grid, c->row_grid), c->ms_grid);
     e = cudaMalloc(&c->partials, size_t(max_grid) * NSTAT * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->dstats, sizeof(DevStats));
     if (e == cudaSuccess) e = cudaMalloc(&c->dflags, sizeof(DevFlags));
@@ -441,7 +478,22 @@ int flbm_step(flbm_ctx *c, int64_t n)
             }
             CK(c, cudaEventRecord(c->ev[2 * c->ev_used], c->stream));
         }
-        if (c->p.scheme == FLBM_LEARNED) {
+        int reduced_grid = c->row_grid > 0 ? c->row_grid : c->grid;   // CTAs that wrote partials
+        if (c->p.state_form == FLBM_STATE_MOMENTS) {
+            if (!c->ms_live) {   // the first collision, from the populations
+                e = launch_ms_boot(static_cast<const float *>(c->g), c->ms[c->ms_cur], make_args<float>(c, t),
+                                   c->p.scheme, odd, stats, c->grid, c->stream);
+                reduced_grid = c->grid;
+                c->ms_live = true;
+            } else {
+                e = launch_ms_step(c->ms[c->ms_cur], c->ms[c->ms_cur ^ 1], make_args<float>(c, t - 1),
+                                   make_args<float>(c, t), c->p.scheme, stats, c->ms_grid, c->ms_zseg,
+                                   c->stream);
+                reduced_grid = c->ms_grid;
+                c->ms_cur ^= 1;
+            }
+            c->pops_valid = false;
+        } else if (c->p.scheme == FLBM_LEARNED) {
             if (!c->mlp_img) return fail(c, FLBM_E_INVALID, "set the network (flbm_set_mlp) before stepping");
             const double w[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
             LearnArgs L;
@@ -467,8 +519,7 @@ int flbm_step(flbm_ctx *c, int64_t n)
             ++c->ev_used;
         }
         if (stats) {
-            e = launch_stats_finalize(c->partials, c->row_grid > 0 ? c->row_grid : c->grid, c->dstats,
-                                      t, double(c->n), c->stream);
+            e = launch_stats_finalize(c->partials, reduced_grid, c->dstats, t, double(c->n), c->stream);
             if (e != cudaSuccess) return fail(c, FLBM_E_CUDA, std::string("stats launch: ") + cudaGetErrorString(e));
         }
     }
@@ -489,6 +540,7 @@ int flbm_step(flbm_ctx *c, int64_t n)
 int flbm_moments(flbm_ctx *c, double *rho, double *j, double *pi)
 {
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (int rc = materialise(c)) return rc;
     const BoxDesc b = box_of(c);
     const uint64_t N = c->n;
     const int prec = prec_code(c);
@@ -552,6 +604,7 @@ int flbm_structure_factor(flbm_ctx *c, int observable, int nshell, double *S, in
     if (observable < FLBM_OBS_RHO || observable > FLBM_OBS_JZ) return fail(c, FLBM_E_INVALID, "unknown observable");
     if (nshell < 1 || nshell > 3072) return fail(c, FLBM_E_INVALID, "nshell must be in [1, 3072]");
     if (!S || !count) return fail(c, FLBM_E_INVALID, "S and count must not be NULL");
+    if (int rc = materialise(c)) return rc;
     const bool dbl = c->p.precision == FLBM_FP64;
     const size_t rs = dbl ? sizeof(double) : sizeof(float);
     const uint64_t nspec = uint64_t(c->p.nx / 2 + 1) * c->p.ny * c->p.nz;
@@ -595,6 +648,7 @@ int flbm_get_populations(flbm_ctx *c, double *f)
 {
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
     if (!f) return fail(c, FLBM_E_INVALID, "f is NULL");
+    if (int rc = materialise(c)) return rc;
     const BoxDesc b = box_of(c);
     const uint64_t N = c->n;
     const int prec = prec_code(c);
@@ -654,6 +708,7 @@ int flbm_set_populations(flbm_ctx *c, const double *f)
         });
     if (rc) return rc;
     c->phase = int(c->step & 1);   // natural form at the current step
+    populations_written(c);
     rc = reset_flags(c);
     if (rc) return rc;
     CK(c, cudaStreamSynchronize(c->stream));
@@ -668,6 +723,7 @@ int flbm_init_thermal(flbm_ctx *c, uint64_t seed)
     b.parity = 0;
     CK(c, launch_init_thermal(c->g, prec_code(c), b, c->p.kT, seed, c->stream));
     c->phase = int(c->step & 1);   // natural form at the current step
+    populations_written(c);
     int rc = reset_flags(c);
     if (rc) return rc;
     CK(c, cudaStreamSynchronize(c->stream));
@@ -681,6 +737,7 @@ int flbm_probe(flbm_ctx *c, const int64_t *nodes, int64_t count, double *f)
     for (int64_t k = 0; k < count; ++k)
         if (nodes[k] < 0 || uint64_t(nodes[k]) >= c->n)
             return fail(c, FLBM_E_INVALID, "probe node index out of range");
+    if (int rc = materialise(c)) return rc;
     int rc = ensure_pipe(c);
     if (rc) return rc;
     const BoxDesc b = box_of(c);
@@ -702,6 +759,7 @@ int flbm_get_state(flbm_ctx *c, void *host)
 {
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
     if (!host) return fail(c, FLBM_E_INVALID, "host is NULL");
+    if (int rc = materialise(c)) return rc;
     const size_t es = elem_size(c->p.precision);
     if (parity(c) == 0) {
         CK(c, cudaMemcpyAsync(host, c->g, c->g_bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -729,6 +787,7 @@ int flbm_set_state(flbm_ctx *c, const void *host)
     if (int rc = replica_state_check(c)) return rc;
     CK(c, cudaMemcpyAsync(c->g, host, c->g_bytes, cudaMemcpyHostToDevice, c->stream));
     c->phase = int(c->step & 1);
+    populations_written(c);
     int rc = reset_flags(c);
     if (rc) return rc;
     CK(c, cudaStreamSynchronize(c->stream));
@@ -755,6 +814,7 @@ int flbm_mlp_pairs(flbm_ctx *c, float *dev_x, float *dev_t)
     if (!is_device_memory(dev_x) || !is_device_memory(dev_t))
         return fail(c, FLBM_E_INVALID, "dev_x and dev_t must be device (or managed) memory");
     if (!(c->p.kT > 0.0)) return fail(c, FLBM_E_INVALID, "training pairs need kT > 0 (the feature scale)");
+    if (int rc = materialise(c)) return rc;
     int rc = ensure_pipe(c);
     if (rc) return rc;
     const BoxDesc b = box_of(c);
@@ -801,6 +861,10 @@ int flbm_set_step(flbm_ctx *c, int64_t step)
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
     if (step < 0) return fail(c, FLBM_E_INVALID, "step must be >= 0");
     if (c->ens) return fail(c, FLBM_E_INVALID, "an ensemble replica follows the ensemble's step");
+    // the moment state's noise is keyed on the step it was made at: continue
+    // from the populations
+    if (int rc = materialise(c)) return rc;
+    populations_written(c);
     const int par = parity(c);
     c->step = step;
     c->phase = int((par - (step & 1)) & 1);

@@ -63,6 +63,15 @@ struct flbm_ctx {
     flbm_ensemble *ens = nullptr;
     // FLBM_LEARNED: the network image on the device (flbm_set_mlp)
     unsigned char *mlp_img = nullptr;
+    // FLBM_STATE_MOMENTS: two arrays of kMsVals * n floats; ms[ms_cur] holds
+    // the state of collision step - 1 while ms_live; the populations in g
+    // are current while pops_valid (at least one of the two holds)
+    float *ms[2] = {nullptr, nullptr};
+    int ms_cur = 0;
+    bool ms_live = false;
+    bool pops_valid = true;
+    int ms_grid = 1;               // CTAs of the moment-state step (one per SM)
+    int ms_zseg = 1;               // z planes a CTA marches per work item
     std::string err;
 };
 

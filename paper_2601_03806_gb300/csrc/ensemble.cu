@@ -99,6 +99,8 @@ std::string validate_ensemble(const flbm_params *params, int count)
             return "replica " + std::to_string(r) +
                    ": scheme, precision, stats_every and seed must match replica 0";
         if (p.scheme > FLBM_REG) return "replica " + std::to_string(r) + ": the ensemble runs BGK, GMF or Reg";
+        if (p.state_form != FLBM_STATE_POPULATIONS)
+            return "replica " + std::to_string(r) + ": the ensemble keeps populations (state_form 0)";
         if (p.nx % 32 != 0) return "replica " + std::to_string(r) + ": nx must be a multiple of 32";
         if (size_t(2) * kQ * size_t(p.nx) * elem_bytes(p.precision) > kMaxStageBytes)
             return "replica " + std::to_string(r) + ": nx too large for two shared-memory stages";

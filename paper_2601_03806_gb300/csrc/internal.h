@@ -155,6 +155,19 @@ void set_thread_error(const char *msg);
 #include <vector>
 
 namespace flbm {
+// Moment-state form (mstate.cu): ten FP32 numbers per node between steps,
+// kMsVals arrays of N: rho - rho0, j_x, j_y, j_z, Q_xx, Q_yy, Q_zz, Q_xy,
+// Q_xz, Q_yz.  ms_prepare sets the kernels' shared-memory attribute and
+// picks the grid and the z-segment length; the noise arguments an name step
+// t - 1, the collision arguments ac step t.
+constexpr int kMsVals = 10;
+cudaError_t ms_prepare(int scheme, int nsm, const StepArgs<float> &a, int &grid, int &zseg);
+cudaError_t launch_ms_boot(const float *g, float *ms, const StepArgs<float> &a, int scheme, bool odd, bool stats,
+                           int grid, cudaStream_t s);
+cudaError_t launch_ms_step(const float *ms_in, float *ms_out, const StepArgs<float> &an, const StepArgs<float> &ac,
+                           int scheme, bool stats, int grid, int zseg, cudaStream_t s);
+cudaError_t launch_ms_export(const float *ms, float *g, const StepArgs<float> &an, int scheme, int grid, int zseg,
+                             cudaStream_t s);
 // Learned-collision network: the bf16 image of weights and split biases in
 // the tensor-core operand layout (mlp_tc.cuh, mlp_infer.cu) from the flat
 // FP32 parameter vector of include/flbm.h (FLBM_MLP_NPARAM values).

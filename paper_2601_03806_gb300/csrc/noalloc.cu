@@ -97,6 +97,8 @@ extern "C" int flbm_step_noalloc(const flbm_params *p, void *dev_state, int64_t 
         return noalloc_fail(FLBM_E_INVALID, "invalid parameters");
     if (p->precision != FLBM_FP32)
         return noalloc_fail(FLBM_E_UNSUPPORTED, "flbm_step_noalloc serves FP32 storage only");
+    if (p->state_form != FLBM_STATE_POPULATIONS)
+        return noalloc_fail(FLBM_E_UNSUPPORTED, "flbm_step_noalloc steps population storage only");
     if (reinterpret_cast<uintptr_t>(dev_state) % 256 != 0)
         return noalloc_fail(FLBM_E_INVALID, "dev_state must be 256-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);

@@ -192,15 +192,35 @@ __device__ __forceinline__ void draw_noise(const A &a, uint32_t node, R (&nz)[kN
 }
 
 // ---------------------------------------------------------------------------
-// a2-a7, a9: collision of one node.  v[cx+1][cy+1][cz+1] holds the incoming
-// deviations on entry and the post-collision deviations on exit.
-// PREDRAWN: nz holds the node's scaled normals (draw_noise, drawn before the
-// populations arrived); otherwise the normals of `node` are drawn here pair
-// by pair and folded in at once (fewer live registers).
+// Maxwell-Boltzmann coefficient rho u_x^i u_y^j u_z^k of mode (i, j, k),
+// order >= 1, as j_first * (the remaining u factors).
+template <typename R>
+__device__ __forceinline__ R aeq_coef(int i, int j, int k, const R (&jj)[3], const R (&uu)[3])
+{
+    const int first = i ? 0 : (j ? 1 : 2);
+    R aeq = jj[first];
+    const int rest[3] = {i - (first == 0), j - (first == 1), k - (first == 2)};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+        for (int e = 0; e < rest[ax]; ++e) aeq *= uu[ax];
+    return aeq;
+}
 
-template <typename R, int SCHEME, bool STATS, bool PREDRAWN, typename A>
-__device__ __forceinline__ void collide_core(R (&v)[3][3][3], const A &a,
-                                             const R (&nz)[kNoise], uint32_t node, R (&acc)[NSTAT])
+// A product rounded on its own (never fused into a following add), so that a
+// relaxed amplitude has one value whether it stays in registers or is stored
+// and reloaded before its noise is added.
+__device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
+__device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
+
+// a2-a5: forward projection of the incoming deviations v (destroyed), the
+// instability check, the fused reductions, and the deterministic
+// post-collision amplitudes qm in the reconstruction's units, Q = syn_scale
+// * M (noise not yet added); rho is the node's density, dj = (rho - rho0,
+// j_x, j_y, j_z) as projected.
+template <typename R, int SCHEME, bool STATS, typename A>
+__device__ __forceinline__ void collide_modes(R (&v)[3][3][3], const A &a, R (&acc)[NSTAT], R (&qm)[3][3][3],
+                                              R &rho, R (&dj)[4])
 {
     // a2: forward Hermite projection, three 1-D passes
 #pragma unroll
@@ -217,7 +237,7 @@ __device__ __forceinline__ void collide_core(R (&v)[3][3][3], const A &a,
         for (int j = 0; j < 3; ++j) analyse(v[i][j][0], v[i][j][1], v[i][j][2]);
 
     const R drho = v[0][0][0];
-    const R rho = a.rho0 + drho;
+    rho = a.rho0 + drho;
     const R jx = v[1][0][0], jy = v[0][1][0], jz = v[0][0][1];
     const R irho = rcp_(rho);
     const R ux = jx * irho, uy = jy * irho, uz = jz * irho;
@@ -248,7 +268,6 @@ __device__ __forceinline__ void collide_core(R (&v)[3][3][3], const A &a,
 
     // a3-a5: post-collision amplitudes in the reconstruction's units,
     // Q = syn_scale * M.  The pre-collision moments v carry fwd_scale.
-    R qm[3][3][3];
     const R jj[3] = {jx, jy, jz};
     const R uu[3] = {ux, uy, uz};
 #pragma unroll
@@ -266,19 +285,11 @@ __device__ __forceinline__ void collide_core(R (&v)[3][3][3], const A &a,
                 } else if (ord == 1) {
                     q = v[i][j][k] * syn;                       // momentum, conserved
                 } else if (ord == 2 || SCHEME == 2) {
-                    // Maxwell-Boltzmann coefficient rho u_x^i u_y^j u_z^k
-                    // = j_first * (remaining u factors)
-                    const int first = i ? 0 : (j ? 1 : 2);
-                    R aeq = jj[first];
-                    const int rest[3] = {i - (first == 0), j - (first == 1), k - (first == 2)};
-#pragma unroll
-                    for (int ax = 0; ax < 3; ++ax)
-#pragma unroll
-                        for (int e = 0; e < rest[ax]; ++e) aeq *= uu[ax];
+                    const R aeq = aeq_coef(i, j, k, jj, uu);
                     if (ord == 2)   // a_eq + (1 - omega)(m - a_eq) = omega a_eq + lambda m
-                        q = syn * (a.lambda * (v[i][j][k] * unfwd) + a.omega * aeq);
+                        q = mul_rn(syn, a.lambda * (v[i][j][k] * unfwd) + a.omega * aeq);
                     else            // Reg ghosts: a_eq (unit relaxation)
-                        q = syn * aeq;
+                        q = mul_rn(syn, aeq);
                 } else if (SCHEME == 0) {
                     q = (syn * unfwd) * (a.lambda * v[i][j][k]);   // BGK ghosts
                 } else {
@@ -286,7 +297,18 @@ __device__ __forceinline__ void collide_core(R (&v)[3][3][3], const A &a,
                 }
                 qm[i][j][k] = q;
             }
+    dj[0] = drho;
+    dj[1] = jx;
+    dj[2] = jy;
+    dj[3] = jz;
+}
 
+// a6-a7: the node's noise added to the amplitudes qm (destroyed), then the
+// reconstruction into post-collision deviations v.
+template <typename R, bool PREDRAWN, typename A>
+__device__ __forceinline__ void noise_synthesise(R (&qm)[3][3][3], R rho, const A &a, const R (&nz)[kNoise],
+                                                 uint32_t node, R (&v)[3][3][3])
+{
     // a6: M_k += phi_k r_k for k = 4..26 with phi_k = sqrt(rho) amp
     // sqrt(b_k / c_s^2) (amp_h for k = 4..9, amp_g for the ghosts)
     {
@@ -343,6 +365,21 @@ __device__ __forceinline__ void collide_core(R (&v)[3][3][3], const A &a,
         for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int k = 0; k < 3; ++k) v[i][j][k] = qm[i][j][k];
+}
+
+// a2-a7, a9: collision of one node.  v[cx+1][cy+1][cz+1] holds the incoming
+// deviations on entry and the post-collision deviations on exit.
+// PREDRAWN: nz holds the node's scaled normals (draw_noise, drawn before the
+// populations arrived); otherwise the normals of `node` are drawn here pair
+// by pair and folded in at once (fewer live registers).
+template <typename R, int SCHEME, bool STATS, bool PREDRAWN, typename A>
+__device__ __forceinline__ void collide_core(R (&v)[3][3][3], const A &a,
+                                             const R (&nz)[kNoise], uint32_t node, R (&acc)[NSTAT])
+{
+    R qm[3][3][3];
+    R rho, dj[4];
+    collide_modes<R, SCHEME, STATS>(v, a, acc, qm, rho, dj);
+    noise_synthesise<R, PREDRAWN>(qm, rho, a, nz, node, v);
 }
 
 // ---------------------------------------------------------------------------

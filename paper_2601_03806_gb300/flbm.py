@@ -25,6 +25,8 @@ FLBM_E_UNSTABLE, FLBM_E_TIMEOUT, FLBM_E_UNSUPPORTED = -4, -5, -6
  FLBM_OBS_JX, FLBM_OBS_JY, FLBM_OBS_JZ) = range(7)
 SCHEMES = {"bgk": FLBM_BGK, "gmf": FLBM_GMF, "reg": FLBM_REG, "learned": FLBM_LEARNED}
 PRECISIONS = {"fp64": FLBM_FP64, "fp32": FLBM_FP32, "fp16": FLBM_FP16}
+FLBM_STATE_POPULATIONS, FLBM_STATE_MOMENTS = 0, 1
+STATE_FORMS = {"populations": FLBM_STATE_POPULATIONS, "moments": FLBM_STATE_MOMENTS}
 Q = 27
 
 
@@ -32,7 +34,8 @@ class flbm_params(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("scheme", C.c_int32), ("precision", C.c_int32),
                 ("noise_rho0", C.c_int32), ("stats_every", C.c_int32),
-                ("noise_stream", C.c_int32), ("tau", C.c_double), ("kT", C.c_double),
+                ("noise_stream", C.c_int32), ("state_form", C.c_int32),
+                ("tau", C.c_double), ("kT", C.c_double),
                 ("rho0", C.c_double), ("seed", C.c_uint64)]
 
 
@@ -209,7 +212,7 @@ def _ptr(a: np.ndarray):
 
 
 def make_params(nx, ny, nz, tau, kT, rho0=1.0, seed=0, scheme=FLBM_GMF, precision=FLBM_FP32,
-                noise_rho0=False, stats_every=1, noise_stream=0) -> flbm_params:
+                noise_rho0=False, stats_every=1, noise_stream=0, state_form=0) -> flbm_params:
     p = flbm_params()
     lib.flbm_params_init(C.byref(p), nx, ny, nz, tau, kT, rho0, seed,
                          SCHEMES.get(scheme, scheme) if isinstance(scheme, str) else scheme)
@@ -217,6 +220,7 @@ def make_params(nx, ny, nz, tau, kT, rho0=1.0, seed=0, scheme=FLBM_GMF, precisio
     p.noise_rho0 = int(bool(noise_rho0))
     p.stats_every = int(stats_every)
     p.noise_stream = int(noise_stream)
+    p.state_form = STATE_FORMS.get(state_form, state_form) if isinstance(state_form, str) else int(state_form)
     return p
 
 
@@ -327,13 +331,15 @@ class Lattice(_CtxOps):
     """Owning wrapper of one flbm_ctx.
 
     torch_memory=True: the population buffer is a torch CUDA tensor and the
-    work is ordered on torch's current stream (``self.stream``)."""
+    work is ordered on torch's current stream (``self.stream``).
+    state_form="moments" (FP32, GMF or Reg): the box keeps ten numbers per
+    node between steps instead of the populations (FLBM_STATE_MOMENTS)."""
 
     def __init__(self, nx, ny, nz, tau, kT, rho0=1.0, seed=0, scheme=FLBM_GMF,
                  precision=FLBM_FP32, noise_rho0=False, stats_every=1, torch_memory=False,
-                 stream=None, noise_stream=0):
+                 stream=None, noise_stream=0, state_form=0):
         self.params = make_params(nx, ny, nz, tau, kT, rho0, seed, scheme, precision,
-                                  noise_rho0, stats_every, noise_stream)
+                                  noise_rho0, stats_every, noise_stream, state_form)
         self.nx, self.ny, self.nz = nx, ny, nz
         self.n = nx * ny * nz
         self._h = C.c_void_p()

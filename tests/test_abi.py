@@ -45,8 +45,9 @@ def test_struct_layout_matches_header(F, tmp_path):
 #include <stddef.h>
 #include "flbm.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\\n", sizeof(flbm_params), offsetof(flbm_params, tau),
-         offsetof(flbm_params, seed), sizeof(flbm_stats_t), offsetof(flbm_stats_t, er));
+  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(flbm_params), offsetof(flbm_params, tau),
+         offsetof(flbm_params, seed), sizeof(flbm_stats_t), offsetof(flbm_stats_t, er),
+         offsetof(flbm_params, state_form));
   return 0;
 }
 """)
@@ -55,7 +56,7 @@ int main(void) {
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                            check=True).stdout.split()]
     assert vals == [C.sizeof(F.flbm_params), F.flbm_params.tau.offset, F.flbm_params.seed.offset,
-                    C.sizeof(F.flbm_stats_t), F.flbm_stats_t.er.offset]
+                    C.sizeof(F.flbm_stats_t), F.flbm_stats_t.er.offset, F.flbm_params.state_form.offset]
 
 
 @pytest.mark.parametrize("kw,code", [
@@ -133,6 +134,27 @@ def test_ensemble_validation_before_device(F, kw, count, code):
     assert rc == code
     assert not e.value
     assert F.flbm_ensemble_last_error(None)
+
+
+@pytest.mark.parametrize("scheme,precision,form", [
+    (0, 1, 1),     # BGK's ghosts keep a memory: no moment state
+    (3, 1, 1),     # nor the learned collision
+    (1, 0, 1),     # FP32 only
+    (2, 2, 1),
+    (1, 1, 2),     # unknown form
+    (1, 1, -1),
+])
+def test_state_form_is_validated(F, scheme, precision, form):
+    p = F.make_params(8, 8, 8, 0.8, 1e-5, scheme=scheme, precision=precision, state_form=form)
+    h = C.c_void_p()
+    assert F.flbm_create_ex(C.byref(p), None, 0, None, C.byref(h)) == F.FLBM_E_INVALID
+    assert not h.value
+    assert b"state_form" in F.flbm_last_error(None) or b"moment-state" in F.flbm_last_error(None)
+    ps = _ens_params(F, 2, {1: dict(state_form=1)})
+    arr = (F.flbm_params * 2)(*ps)
+    e = C.c_void_p()
+    assert F.flbm_ensemble_create(arr, 2, None, C.byref(e)) == F.FLBM_E_INVALID
+    assert not e.value
 
 
 def test_noise_stream_is_validated(F):
