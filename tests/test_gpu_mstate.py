@@ -63,6 +63,27 @@ def test_matches_population_form_bit_for_bit(F, scheme, shape):
     b.close()
 
 
+@pytest.mark.parametrize("kw", [dict(noise_rho0=True), dict(stats_every=3), dict(kT=0.0),
+                                dict(torch_memory=True), dict(rho0=1.3, tau=2.5)])
+def test_variants_match_population_form(F, kw):
+    """Local or reference density in the noise amplitude, reductions every
+    third step, no noise, a torch-owned population buffer, another density
+    and viscosity."""
+    shape = (34, 16, 7)
+    args = dict(tau=0.9, kT=2e-4, seed=12, scheme=1, precision=F.FLBM_FP32, noise_stream=3)
+    args.update(kw)
+    a = F.Lattice(*shape, state_form=F.FLBM_STATE_POPULATIONS, **args)
+    b = F.Lattice(*shape, state_form=F.FLBM_STATE_MOMENTS, **args)
+    for lat in (a, b):
+        lat.init_thermal(4)
+    a.step(8)
+    b.step(8)
+    assert np.array_equal(a.get_state(), b.get_state())
+    sa, sb = a.stats(), b.stats()
+    assert sa["n_samples"] == sb["n_samples"]
+    assert np.allclose(sa["u2_avg"], sb["u2_avg"], rtol=1e-6, atol=1e-30)
+
+
 def test_reads_between_steps_do_not_change_the_run(F):
     shape = (45, 17, 12)
     ref = box(F, shape, 1, F.FLBM_STATE_POPULATIONS)
