@@ -15,13 +15,18 @@
 //
 // k_ms_step: a CTA owns a column of 30 x 14 (x, y) nodes and marches along
 // z.  Each of its 512 threads owns one node of the column's 32 x 16 halo
-// footprint: per plane it loads that node's ten numbers, adds its noise and
-// reconstructs its 27 post-collision populations (collide_core's second
-// half, the same code) into a ring of three planes in shared memory.  The
-// 420 interior threads then pull their 27 incoming populations from the
-// ring and collide (collide_core's first half) into the next state.  The
-// halo is recomputed by the neighbouring columns (512 / 420 = 1.22 times the
-// reconstruction work); the ten loads per halo node mostly hit L2.
+// footprint (warp w = footprint row w): per plane it loads that node's ten
+// numbers, adds its noise and reconstructs its 27 post-collision populations
+// (collide_core's second half, the same code) into a ring of four planes in
+// shared memory.  The 420 interior threads then pull their 27 incoming
+// populations from the ring and collide (collide_core's first half) into
+// the next state; the two all-halo warps skip the pull.  The halo is
+// recomputed by the neighbouring columns (512 / 420 = 1.22 times the
+// reconstruction work); the ten loads per halo node mostly hit L2.  With
+// four planes in the ring, the plane a thread overwrites was last pulled two
+// planes earlier, before the previous barrier, so one barrier per plane
+// suffices and warps run from one plane's pull straight into the next
+// plane's reconstruction.
 //
 // k_ms_boot: the first collision from a population state (any state,
 // including one with ghost content); k_ms_step<EXPORT>: the populations of
@@ -37,8 +42,9 @@ namespace {
 
 constexpr int kMsTX = 30, kMsTY = 14;                      // interior of a column
 constexpr int kMsHX = kMsTX + 2, kMsHY = kMsTY + 2;        // with the halo: 32 x 16
-constexpr int kMsThreads = kMsHX * kMsHY;                  // one halo node per thread
-constexpr size_t kMsRingBytes = size_t(3) * kQ * kMsThreads * sizeof(float);   // 165,888 B
+constexpr int kMsThreads = kMsHX * kMsHY;                  // 512: one halo node per thread
+constexpr int kMsSlots = 4;                                // planes in the ring
+constexpr size_t kMsRingBytes = size_t(kMsSlots) * kQ * kMsThreads * sizeof(float);   // 221,184 B
 
 // the six second-order modes in state order: xx, yy, zz, xy, xz, yz
 __host__ __device__ constexpr int ord2_deg(int r, int ax)
@@ -145,13 +151,13 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_ms_step(const float *__restri
                                                            const StepArgs<float> an, const StepArgs<float> ac,
                                                            const MsGeom geo)
 {
-    extern __shared__ __align__(16) float ring[];   // [3][27][512]
+    extern __shared__ __align__(16) float ring[];   // [4][27][512]
     float acc[NSTAT];
 #pragma unroll
     for (int s = 0; s < NSTAT; ++s) acc[s] = 0.0f;
     const I N = I(an.n);
     const uint32_t nx = an.nx, ny = an.ny, nz = an.nz;
-    const uint32_t hx = threadIdx.x & (kMsHX - 1), hy = threadIdx.x / kMsHX;
+    const uint32_t hx = threadIdx.x % kMsHX, hy = threadIdx.x / kMsHX;
     for (uint64_t item = blockIdx.x; item < geo.items; item += gridDim.x) {
         const uint32_t tx = uint32_t(item % geo.ntx);
         const uint64_t rest = item / geo.ntx;
@@ -165,7 +171,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_ms_step(const float *__restri
         const I col = I(xg) + I(nx) * I(yg);
         const I plane = I(nx) * I(ny);
         // plane m of the march is z0 - 1 + m (periodic), held in ring slot m
-        // % 3; its state is loaded one plane ahead (in flight during the
+        // % 4; its state is loaded one plane ahead (in flight during the
         // previous plane's pull) into st
         const uint32_t last = z1 - z0 + 1;
         auto node_of = [&](uint32_t m) { return col + I((z0 + m + nz - 1) % nz) * plane; };
@@ -173,7 +179,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_ms_step(const float *__restri
         auto build = [&](uint32_t m) {
             float v[3][3][3];
             rebuild<SCHEME>(st, uint32_t(node_of(m)), an, v);
-            float *slot = ring + size_t(m % 3) * kQ * kMsThreads + threadIdx.x;
+            float *slot = ring + size_t(m % kMsSlots) * kQ * kMsThreads + threadIdx.x;
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_ms_step(const float *__restri
                     for (int j = 0; j < 3; ++j)
 #pragma unroll
                         for (int k = 0; k < 3; ++k) {
-                            const uint32_t src = (m + 4 - k) % 3;   // plane m - (k - 1)
+                            const uint32_t src = (m + 1 - k) % kMsSlots;   // plane m - (k - 1)
                             const uint32_t pos = (hy + 1 - j) * kMsHX + (hx + 1 - i);
                             v[i][j][k] = ring[(size_t(src) * kQ + 9 * i + 3 * j + k) * kMsThreads + pos];
                         }
@@ -217,8 +223,8 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_ms_step(const float *__restri
                     store_state(out, N, n, qm, dj);
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();   // the next item's first planes reuse the ring
     }
     if (STATS) block_reduce_store(acc, ac.partials + size_t(blockIdx.x) * NSTAT);
 }
@@ -282,12 +288,12 @@ cudaError_t ms_prepare(int scheme, int nsm, const StepArgs<float> &a, int &grid,
     const cudaError_t e = scheme == FLBM_REG ? set_attrs<FLBM_REG>() : set_attrs<FLBM_GMF>();
     if (e != cudaSuccess) return e;
     // z segments: long enough that the two extra halo planes per segment cost
-    // little (<= 64 planes: 3 %), short enough for about eight columns-segments
-    // per CTA
+    // little (<= 128 planes: 1.6 %), short enough for about eight
+    // column segments per CTA
     const uint64_t cols = uint64_t((a.nx + kMsTX - 1) / kMsTX) * ((a.ny + kMsTY - 1) / kMsTY);
     const uint64_t want = uint64_t(8) * uint64_t(nsm);
     uint64_t z = (cols * a.nz + want - 1) / want;
-    zseg = int(std::max<uint64_t>(8, std::min<uint64_t>(64, z)));
+    zseg = int(std::max<uint64_t>(8, std::min<uint64_t>(128, z)));
     zseg = int(std::min<uint64_t>(uint64_t(zseg), a.nz));
     grid = int(std::min<uint64_t>(geometry(a, zseg).items, uint64_t(nsm)));   // one CTA per SM (shared ring)
     if (grid < 1) grid = 1;

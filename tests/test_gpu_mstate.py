@@ -40,7 +40,8 @@ def box(F, shape, scheme, form, tau=0.8, kT=1e-4, seed=31, stats_every=1, stream
                      stats_every=stats_every, noise_stream=stream, state_form=form)
 
 
-SHAPES = [(37, 19, 5), (30, 14, 3), (1, 1, 1), (64, 2, 9), (5, 31, 70), (61, 29, 2)]
+SHAPES = [(37, 19, 5), (30, 14, 3), (32, 13, 3), (1, 1, 1), (64, 2, 9), (5, 31, 70), (61, 29, 2),
+          (96, 27, 130)]
 
 
 @pytest.mark.parametrize("scheme", [1, 2])
@@ -169,8 +170,8 @@ def test_full_size_sampled_nodes(F, O):
     pts = rng.integers(0, n, size=(40, 3))
     pts[0] = (0, 0, 0)
     pts[1] = (n - 1, n - 1, n - 1)
-    pts[2] = (29, 13, 63)                  # a column corner and a z-segment end
-    pts[3] = (30, 14, 64)
+    pts[2] = (29, 13, 127)                 # a column corner and a z-segment end
+    pts[3] = (30, 14, 128)
     g.step(2)                              # boot + one moment step
     s1 = g.stats()                         # reductions of step 1
     for t_check in (2, 3):
