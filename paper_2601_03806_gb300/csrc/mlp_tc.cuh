@@ -58,12 +58,17 @@ constexpr size_t kMlpSmemBytes = (sizeof(MlpSmem) + 1023) / 1024 * 1024;
 
 // silu(z) = z sigmoid(z) = hz (1 + tanh(hz)) with hz = z / 2, from hz, with
 // the hardware tanh (absolute error about 2^-11, below the bf16 rounding of
-// the activations).
-__device__ __forceinline__ float silu_half(float hz)
+// the activations); two activations at a time, the FMA as one packed FP32
+// pair (each lane rounded as the scalar FMA would be).
+__device__ __forceinline__ void silu_half2(float &a, float &b)
 {
-    float t;
-    asm("tanh.approx.f32 %0, %1;\n" : "=f"(t) : "f"(hz));
-    return __fmaf_rn(hz, t, hz);
+    float ta, tb;
+    asm("tanh.approx.f32 %0, %1;\n" : "=f"(ta) : "f"(a));
+    asm("tanh.approx.f32 %0, %1;\n" : "=f"(tb) : "f"(b));
+    const float2 h = make_float2(a, b);
+    const float2 r = __ffma2_rn(h, make_float2(ta, tb), h);
+    a = r.x;
+    b = r.y;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
@@ -191,7 +196,7 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
             float z[16];
             tmem_ld16(tmem + lane_base + 16 * ch, z);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) z[i] = silu_half(z[i]);
+            for (int i = 0; i < 16; i += 2) silu_half2(z[i], z[i + 1]);
             store_row16(a2p, kSbo64, t, 16 * ch, z);
         }
         mlp_sync_for_mma(q);
@@ -214,7 +219,7 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
             float z[16];
             tmem_ld16(tmem + lane_base + 64 + 16 * ch, z);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) z[i] = silu_half(z[i]);
+            for (int i = 0; i < 16; i += 2) silu_half2(z[i], z[i + 1]);
             store_row16(a2p, kSbo64, t, 16 * ch, z);
         }
         mlp_sync_for_mma(q);

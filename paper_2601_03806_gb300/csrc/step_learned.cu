@@ -160,33 +160,48 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_step_learned(float *__restri
         if (!cur.active) continue;
         const Nbr<I> nb(cur.x, cur.y, cur.z, a.nx, a.ny, a.nz);
         const I n = nb.node();
-        // correction d_c = w_c sigma^3 y_c, minus its mass and momentum
+        // correction d_c = w_c sigma^3 y_c minus its mass and momentum:
+        // P(d)_c = d_c - w_c (alpha + 3 c . beta), alpha = sum d, beta = sum c d,
+        // with the sums and the 27 offsets taken axis by axis
         float d[3][3][3];
-        float alpha = 0.0f, bx = 0.0f, by = 0.0f, bz = 0.0f;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = 0; j < 3; ++j)
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const float w = float(w1(i - 1) * w1(j - 1) * w1(k - 1));
-                    const float dv = w * L.sig3 * yv[slot_of(i - 1, j - 1, k - 1)];
-                    d[i][j][k] = dv;
-                    alpha += dv;
-                    bx += dv * float(i - 1);
-                    by += dv * float(j - 1);
-                    bz += dv * float(k - 1);
-                }
+                for (int k = 0; k < 3; ++k)
+                    d[i][j][k] = (float(w1(i - 1) * w1(j - 1) * w1(k - 1)) * L.sig3) * yv[slot_of(i - 1, j - 1, k - 1)];
+        float T[3][3], bz = 0.0f;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j)
+            for (int j = 0; j < 3; ++j) {
+                T[i][j] = (d[i][j][0] + d[i][j][2]) + d[i][j][1];
+                bz += d[i][j][2] - d[i][j][0];
+            }
+        float Sx[3], by = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            Sx[i] = (T[i][0] + T[i][2]) + T[i][1];
+            by += T[i][2] - T[i][0];
+        }
+        const float alpha = (Sx[0] + Sx[2]) + Sx[1];
+        const float bx = Sx[2] - Sx[0];
+        const float b3[3] = {3.0f * bx, 3.0f * by, 3.0f * bz};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float ti = i == 1 ? alpha : (i == 2 ? alpha + b3[0] : alpha - b3[0]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float tij = j == 1 ? ti : (j == 2 ? ti + b3[1] : ti - b3[1]);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
+                    const float t = k == 1 ? tij : (k == 2 ? tij + b3[2] : tij - b3[2]);
                     const float w = float(w1(i - 1) * w1(j - 1) * w1(k - 1));
-                    const float cb = bx * float(i - 1) + by * float(j - 1) + bz * float(k - 1);
-                    v[i][j][k] += d[i][j][k] - w * (alpha + 3.0f * cb);
+                    v[i][j][k] += __fmaf_rn(-w, t, d[i][j][k]);
                 }
+            }
+        }
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
