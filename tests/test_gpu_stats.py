@@ -172,3 +172,38 @@ def test_spectral_er_gmf_vs_reg_same_noise(F, oracle_mod):
         assert 0.85 < lo and hi < 1.15, (m, lo, hi)
         sel = slice(4, 21)
         assert np.abs(er_g[sel] - er_r[sel]).max() < 0.03, (m, er_g[sel], er_r[sel])
+
+
+def test_smallest_viscosity_bgk_fails_gmf_and_reg_hold(F, oracle_mod):
+    """Sec. III at the paper's smallest viscosity, tau = 0.5001, and its
+    kT = 1/3000 (scaled to 48^3): BGK-FLBM, whose ghost modes relax with
+    omega close to 2, goes unstable within a few hundred steps, while
+    GMF-FLBM and Reg-FLBM stay stable.  Driven by the same noise, their
+    spectral ER curves coincide (max difference < 0.01 on shells 4..20) and
+    stay near 1 with the mild overestimation the paper reports at the
+    smallest viscosities (observed 0.90..1.24)."""
+    from paper_2601_03806_gb300 import analysis
+    n, kT, rho0, tau = 48, 1.0 / 3000.0, 1.0, 0.5001
+    g = F.Lattice(n, n, n, tau, kT, rho0=rho0, seed=2601, scheme=0, precision=1, stats_every=0)
+    g.set_state(thermal_state(oracle_mod, n, kT, rho0, seed=5))
+    with pytest.raises(F.FlbmError) as ei:
+        g.step(400)
+    assert ei.value.code == F.FLBM_E_UNSTABLE
+    assert 0 < g.step_count < 400
+    g.close()
+    curves = {}
+    for scheme in (1, 2):
+        g = F.Lattice(n, n, n, tau, kT, rho0=rho0, seed=2601, scheme=scheme, precision=1,
+                      stats_every=0)
+        g.set_state(thermal_state(oracle_mod, n, kT, rho0, seed=5))
+        g.step(100)
+        curves[scheme] = analysis.er_spectrum(g, 28, snapshots=30, every=10)
+        assert g.step_count == 400
+        g.close()
+    for m in analysis.PAPER_OBSERVABLES:
+        er_g, cnt = curves[1][m]
+        er_r, _ = curves[2][m]
+        lo, hi = analysis.window_extrema(er_g, cnt, 4, 20)
+        assert 0.85 < lo and hi < 1.3, (m, lo, hi)
+        sel = slice(4, 21)
+        assert np.abs(er_g[sel] - er_r[sel]).max() < 0.01, (m, er_g[sel], er_r[sel])
