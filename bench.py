@@ -478,25 +478,31 @@ def run_ours(args, rank, local, ws):
             hrho = torch.empty(N, dtype=torch.float64, pin_memory=True)
             hj = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
             hpi = torch.empty(6 * N, dtype=torch.float64, pin_memory=True)
-        torch.cuda.synchronize()
-        barrier(ws)
-        t0 = time.perf_counter()
-        lat.set_state(hstate)
-        t1 = time.perf_counter()
-        lat.set_step(args.warmup)
-        for _ in range(args.steps):
-            lat.step(1)
-            lat.stats()
-        t2 = time.perf_counter()
-        if with_moments:
-            rc = flbm.flbm_moments(lat.handle, hrho.data_ptr(), hj.data_ptr(), hpi.data_ptr())
-            if rc != 0:
-                raise RuntimeError(flbm.flbm_last_error(lat.handle))
-        torch.cuda.synchronize()
-        t3 = time.perf_counter()
-        e_ms = (t3 - t0) * 1e3
-        e2e_split = {"upload_ms": (t1 - t0) * 1e3, "steps_ms": (t2 - t1) * 1e3,
-                     "snapshot_ms": (t3 - t2) * 1e3}
+        # the whole end-to-end pass three times (the host link is shared with
+        # other work on the machine, so one upload can be several times
+        # slower than the next); the line reports the median pass
+        passes = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            barrier(ws)
+            t0 = time.perf_counter()
+            lat.set_state(hstate)
+            t1 = time.perf_counter()
+            lat.set_step(args.warmup)
+            for _ in range(args.steps):
+                lat.step(1)
+                lat.stats()
+            t2 = time.perf_counter()
+            if with_moments:
+                rc = flbm.flbm_moments(lat.handle, hrho.data_ptr(), hj.data_ptr(), hpi.data_ptr())
+                if rc != 0:
+                    raise RuntimeError(flbm.flbm_last_error(lat.handle))
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            passes.append(((t3 - t0) * 1e3, {"upload_ms": (t1 - t0) * 1e3, "steps_ms": (t2 - t1) * 1e3,
+                                              "snapshot_ms": (t3 - t2) * 1e3}))
+        passes.sort(key=lambda p: p[0])
+        e_ms, e2e_split = passes[1]
         e_max = max_over_ranks(e_ms, ws, dev)
         import ctypes
         stats_bytes = ctypes.sizeof(flbm.flbm_stats_t) + 16
@@ -505,7 +511,8 @@ def run_ours(args, rank, local, ws):
                "d2h_bytes_per_step": (mom_bytes if with_moments else 0) // args.steps + stats_bytes,
                "what": "flbm_set_state from pinned host + K x (flbm_step(1) + flbm_stats)"
                        + (" + flbm_moments snapshot to pinned host" if with_moments else ""),
-               "split": e2e_split, "host_placement": numa}
+               "split": e2e_split, "host_placement": numa,
+               "passes_ms": [p[0] for p in passes], "reported": "median of 3 passes"}
         del hstate
 
     cpu = None

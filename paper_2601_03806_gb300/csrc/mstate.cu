@@ -100,7 +100,9 @@ __device__ __forceinline__ void rebuild(const float (&st)[kMsVals], uint32_t nod
 #pragma unroll
     for (int r = 0; r < 6; ++r) qm[ord2_deg(r, 0)][ord2_deg(r, 1)][ord2_deg(r, 2)] = st[4 + r];
     float nzd[kNoise];   // unused: drawn inside
-    noise_synthesise<float, false>(qm, rho, an, nzd, node, v);
+    // scalar passes (the same bits as the paired ones; faster in this
+    // kernel's register budget, measured)
+    noise_synthesise<float, false, false>(qm, rho, an, nzd, node, v);
 }
 
 template <bool ODD, int SCHEME, bool STATS, typename I>
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_ms_step(const float *__restri
                             for (int k = 0; k < 3; ++k) out[I(slot_of(i - 1, j - 1, k - 1)) * N + n] = v[i][j][k];
                 } else {
                     float qm[3][3][3], rho, dj[4];
-                    collide_modes<float, SCHEME, STATS>(v, ac, acc, qm, rho, dj);
+                    collide_modes<float, SCHEME, STATS, false>(v, ac, acc, qm, rho, dj);
                     store_state(out, N, n, qm, dj);
                 }
             }
