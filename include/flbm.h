@@ -146,7 +146,9 @@ int flbm_params_init(flbm_params *p, int nx, int ny, int nz, double tau, double 
                      double rho0, uint64_t seed, int scheme);
 
 /* Device bytes the population state needs (27 N elements of the storage
- * type, AA-pattern in place).  0 on invalid parameters. */
+ * type, AA-pattern in place).  0 on invalid parameters.  A moment-state
+ * context (state_form = FLBM_STATE_MOMENTS) also allocates 2 x 10 N floats
+ * of its own, which dev_buf does not cover. */
 size_t flbm_state_bytes(const flbm_params *p);
 
 /* Create a context with flbm_params_init defaults: FP32 deviations, AA in
@@ -166,7 +168,9 @@ int flbm_create_ex(const flbm_params *p, void *dev_buf, size_t dev_bytes,
 
 /* Advance n >= 0 steps (Eq. flbe2 / flbe per the scheme; one fused
  * stream-and-collide kernel per step, reductions on the steps selected by
- * stats_every).  Returns FLBM_E_UNSTABLE if any step met rho <= 0 or a
+ * stats_every; in the moment-state form the first step after the
+ * populations were written collides from them, later ones from the ten
+ * numbers per node).  Returns FLBM_E_UNSTABLE if any step met rho <= 0 or a
  * non-finite density; the step counter is then the t of the first such
  * step and the populations hold that step's output (restore a checkpoint). */
 int flbm_step(flbm_ctx *c, int64_t n);
