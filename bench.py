@@ -696,22 +696,28 @@ def run_ensemble(args, rank, local, ws):
         hstates = [torch.empty(27 * rep.n, dtype=torch.float32, pin_memory=True) for rep in ens.replicas]
         for rep, h in zip(ens.replicas, hstates):
             rep.get_state(h)
-        torch.cuda.synchronize()
-        barrier(ws)
-        t0 = time.perf_counter()
-        for rep, h in zip(ens.replicas, hstates):
-            rep.set_state(h)
-        ens.step(args.steps)
-        stats = [rep.stats() for rep in ens.replicas]
-        torch.cuda.synchronize()
-        e_ms = (time.perf_counter() - t0) * 1e3
+        # three passes (median reported) when K keeps the storage in the
+        # natural form that a replica's state replacement needs
+        passes = []
+        for _ in range(3 if args.steps % 2 == 0 else 1):
+            torch.cuda.synchronize()
+            barrier(ws)
+            t0 = time.perf_counter()
+            for rep, h in zip(ens.replicas, hstates):
+                rep.set_state(h)
+            ens.step(args.steps)
+            stats = [rep.stats() for rep in ens.replicas]
+            torch.cuda.synchronize()
+            passes.append((time.perf_counter() - t0) * 1e3)
+        e_ms = sorted(passes)[len(passes) // 2]
         e_max = max_over_ranks(e_ms, ws, dev)
         import ctypes
         e2e = {"value": job_mlups(N, args.steps, e_max, ws), "unit": "MLUPS",
                "h2d_bytes_per_step": 4 * 27 * N // args.steps,
                "d2h_bytes_per_step": len(stats) * (ctypes.sizeof(flbm.flbm_stats_t) + 16),
                "what": "flbm_set_state of every replica from pinned host + flbm_ensemble_step(K) + "
-                       "flbm_stats of every replica"}
+                       "flbm_stats of every replica",
+               "passes_ms": passes, "reported": "median of %d passes" % len(passes)}
         del hstates
 
     cpu = None
@@ -877,19 +883,23 @@ def run_learned(args, rank, local, ws):
     if not args.no_e2e:
         hstate = torch.empty(27 * N, dtype=torch.float32, pin_memory=True)
         lat.get_state(hstate)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        lat.set_state(hstate)
-        for _ in range(args.steps):
-            lat.step(1)
-            lat.stats()
-        torch.cuda.synchronize()
-        e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, ws, dev)
+        passes = []
+        for _ in range(3):   # median of three passes, as for the box workload
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lat.set_state(hstate)
+            for _ in range(args.steps):
+                lat.step(1)
+                lat.stats()
+            torch.cuda.synchronize()
+            passes.append((time.perf_counter() - t0) * 1e3)
+        e_ms = max_over_ranks(sorted(passes)[1], ws, dev)
         import ctypes
         e2e = {"value": job_mlups(N, args.steps, e_ms, ws), "unit": "MLUPS",
                "h2d_bytes_per_step": 4 * 27 * N // args.steps,
                "d2h_bytes_per_step": ctypes.sizeof(flbm.flbm_stats_t) + 16,
-               "what": "flbm_set_state from pinned host + K x (flbm_step(1) + flbm_stats)"}
+               "what": "flbm_set_state from pinned host + K x (flbm_step(1) + flbm_stats)",
+               "passes_ms": passes, "reported": "median of 3 passes"}
         del hstate
     stats_learned = statistics(lat)
     lat.close()
