@@ -90,7 +90,7 @@ enum flbm_status {
     FLBM_E_CUDA = -3,        /* a CUDA runtime / cuFFT call failed */
     FLBM_E_UNSTABLE = -4,    /* a step met rho <= 0 or a non-finite value */
     FLBM_E_TIMEOUT = -5,     /* reserved: bounded device wait ran out */
-    FLBM_E_UNSUPPORTED = -6  /* valid request this build does not implement */
+    FLBM_E_UNSUPPORTED = -6  /* valid request the library does not implement */
 };
 
 /* Observables of the equilibration ratio and of S(k) (Sec. III): the local
