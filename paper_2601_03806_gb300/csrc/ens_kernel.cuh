@@ -143,7 +143,10 @@ __device__ __forceinline__ void ens_item(const EnsReplica &rp, uint64_t i, uint3
 // At most 112 registers a thread (the collision spills little at that cap).
 // Registers are split over the SM's four sub-partitions, so two CTAs fit an
 // SM up to 7 compute warps each; two CTAs of 8 + 1 warps would need <= 96.
-template <typename S, typename R, int SCHEME, bool ODD, bool STATS>
+// STRIDE: the stage stride as a compile-time constant (256 or 512 nodes, the
+// common tunings), which folds the 27 segment offsets of a node's shared
+// loads and stores into their immediates; 0 reads it from the arguments.
+template <typename S, typename R, int SCHEME, bool ODD, bool STATS, int STRIDE = 0>
 __global__ void __maxnreg__(112) k_step_ens(const __grid_constant__ EnsArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -152,7 +155,7 @@ __global__ void __maxnreg__(112) k_step_ens(const __grid_constant__ EnsArgs a)
     const EnsReplica *__restrict__ reps = a.reps;
     const uint32_t nc = blockDim.x - 32;                 // compute threads
     const uint32_t stages = a.stages;
-    const uint32_t stride = a.stride;
+    const uint32_t stride = STRIDE ? uint32_t(STRIDE) : a.stride;
     const uint32_t stage_elems = uint32_t(kQ) * stride;
     const uint32_t lane = threadIdx.x & 31;
     uint64_t begin, end;
@@ -346,7 +349,16 @@ cudaError_t launch_ens_step_t(const EnsArgs &a, int scheme, bool odd, bool stats
                               size_t smem, cudaStream_t s)
 {
 #define FLBM_LAUNCH_ENS(SC, OD, ST) k_step_ens<S, R, SC, OD, ST><<<grid, threads, smem, s>>>(a)
-    if (scheme == 0) {
+#define FLBM_LAUNCH_ENS_W(W, OD, ST) k_step_ens<S, R, 1, OD, ST, W><<<grid, threads, smem, s>>>(a)
+    if (scheme == 1 && (a.stride == 512 || a.stride == 256)) {   // GMF at a compile-time stride
+        if (a.stride == 512) {
+            if (odd) { if (stats) FLBM_LAUNCH_ENS_W(512, true, true); else FLBM_LAUNCH_ENS_W(512, true, false); }
+            else     { if (stats) FLBM_LAUNCH_ENS_W(512, false, true); else FLBM_LAUNCH_ENS_W(512, false, false); }
+        } else {
+            if (odd) { if (stats) FLBM_LAUNCH_ENS_W(256, true, true); else FLBM_LAUNCH_ENS_W(256, true, false); }
+            else     { if (stats) FLBM_LAUNCH_ENS_W(256, false, true); else FLBM_LAUNCH_ENS_W(256, false, false); }
+        }
+    } else if (scheme == 0) {
         if (odd) { if (stats) FLBM_LAUNCH_ENS(0, true, true); else FLBM_LAUNCH_ENS(0, true, false); }
         else     { if (stats) FLBM_LAUNCH_ENS(0, false, true); else FLBM_LAUNCH_ENS(0, false, false); }
     } else if (scheme == 1) {
@@ -357,6 +369,7 @@ cudaError_t launch_ens_step_t(const EnsArgs &a, int scheme, bool odd, bool stats
         else     { if (stats) FLBM_LAUNCH_ENS(2, false, true); else FLBM_LAUNCH_ENS(2, false, false); }
     }
 #undef FLBM_LAUNCH_ENS
+#undef FLBM_LAUNCH_ENS_W
     return cudaGetLastError();
 }
 
@@ -370,6 +383,16 @@ int ens_occupancy_scheme(int threads, size_t smem)
     cudaFuncSetAttribute(k_step_ens<S, R, SC, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_step_ens<S, R, SC, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_step_ens<S, R, SC, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (SC == 1) {
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, false, false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, false, true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, true, false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, true, true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, false, false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, false, true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, true, false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, true, true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    }
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_ens<S, R, SC, true, true>, threads, smem) !=
         cudaSuccess)
