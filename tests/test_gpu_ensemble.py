@@ -256,3 +256,45 @@ def test_mixed_workload_sampled_replicas(F, O):
         assert d < 6e-6, (r, d)
         s = ens[r].stats()
         assert s["n_samples"] == 3 and abs(s["mass"] / mass0[r] - 1) < 1e-7
+
+
+def test_fp16_replicas_against_oracle(F, O):
+    """FP16 deviation storage: one step of every replica against the oracle
+    within 2e-5 (the single-box FP16 tolerance: half rounding on load and
+    store of O(1e-2) deviations)."""
+    mix = MIX[:3]
+    ens = F.Ensemble(make_params(F, mix, precision=2))
+    boxes = []
+    for r, (nx, ny, nz, tau, kT, rho0, s) in enumerate(mix):
+        w = O.tables()["w"]
+        f0 = w[:, None, None, None] * (rho0 + 0.02 * inputs.population_perturbation(nx, ny, nz, 60 + r))
+        ens[r].set_populations(f0)
+        o = O.Box(nx, ny, nz, tau, kT, rho0=rho0, seed=SEED, stream=s)
+        o.set_f(ens[r].get_populations())   # the oracle starts from the stored (half-rounded) state
+        boxes.append(o)
+    ens.step(1)
+    for r, o in enumerate(boxes):
+        o.step(1)
+        assert np.abs(ens[r].get_populations() - o.get_f()).max() < 2e-5, r
+
+
+def test_replica_structure_factor_matches_single_box(F):
+    """S(k) of a replica (its borrowed context) against the single box of the
+    same parameters and noise stream: the states agree to a few units in the
+    last place, so the spectra agree to 1e-5 relative."""
+    nx = ny = nz = 32
+    params = [F.make_params(nx, ny, nz, 0.8, 1e-4, seed=SEED, noise_stream=s) for s in (4, 9)]
+    ens = F.Ensemble(params)
+    for r, rep in enumerate(ens.replicas):
+        rep.init_thermal(70 + r)
+    ens.step(6)
+    box = F.Lattice(nx, ny, nz, 0.8, 1e-4, seed=SEED, noise_stream=9)
+    box.init_thermal(71)
+    box.step(6)
+    for obs in range(7):
+        Sa, ca = ens[1].structure_factor(obs, 16)
+        Sb, cb = box.structure_factor(obs, 16)
+        assert np.array_equal(ca, cb)
+        assert np.allclose(Sa, Sb, rtol=1e-5, atol=1e-30), obs
+    box.close()
+    ens.close()
