@@ -10,6 +10,12 @@ measure so the reported <u_a^2> is an equilibrium value.
 Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the host cores instead (bounded sample of the same workload).
 
+Extra lines (not the default): ``--precision fp16`` (FP16 storage),
+``--state-form moments`` (the thread-safe moment-state form, ten numbers per
+node), ``--workload ensemble`` (328 replica boxes in one persistent kernel
+per step) and ``--workload learned`` (GMF-FLBM plus the tensor-core network
+correction on 256^3, with its training and a statistics run).
+
 Multi-GPU: the path runs independent replica boxes, one per rank ("replicas
 only", weak scaling); torch.distributed is used for the barrier and the
 max-over-ranks time only.
