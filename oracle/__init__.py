@@ -13,7 +13,10 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
 * ``feq2``              pinned: moments 0/1/2 exact, zero ghost projection
 * ``noise_term``        pinned: conservation, single-node AR(1) stationary variance
 * ``collide_node/step`` pinned: conservation, AR(1) lag-1 = 1-omega / 0, shear-wave
-                        viscosity, tau=1 GMF == BGK, kT=0 cube-rotation covariance
+                        viscosity, tau=1 GMF == BGK, kT=0 cube-rotation covariance,
+                        uniform-flow equilibrium fixed point at every tau and the
+                        post-collision second and ghost moments of a moving state
+                        (the f^eq subtraction of Eq. moments2)
 * ``REG`` scheme        parity unpinned for its ghost relaxation (the paper does
                         not define Reg-FLBM's ghost non-equilibrium treatment);
                         its full-order equilibrium coefficients are pinned against

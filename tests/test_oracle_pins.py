@@ -287,6 +287,85 @@ def test_reg_full_order_equilibrium_is_product_form(oracle_mod):
     assert np.abs(fs - rho * fac.prod(1)).max() < 1e-16
 
 
+def _feq_second_order(c, w, rho, u):
+    """Second-order Hermite expansion of the Maxwellian (the f^eq that follows
+    Eq. flbe2), written out here from its definition, not the oracle's."""
+    cu = c @ u
+    return w * rho * (1 + cu / CS2 + (cu * cu - CS2 * (u @ u)) / (2 * CS2 * CS2))
+
+
+def _feq_product_form(c, rho, u):
+    """Full-order D3Q27 equilibrium: rho prod_a phi(c_a, u_a), with the D1Q3
+    equilibrium phi(c, u) = w1(c)(1 + c u / c_s^2 + (c^2 - c_s^2) u^2 /
+    (2 c_s^4)), w1(0) = 2/3, w1(+-1) = 1/6 (its moments are 1, u, c_s^2 + u^2
+    on each axis, so every Hermite coefficient is rho u_x^a u_y^b u_z^c)."""
+    w1 = np.where(c == 0, 2.0 / 3.0, 1.0 / 6.0)
+    return rho * (w1 * (1 + c * u / CS2 + (c * c - CS2) * u * u / (2 * CS2 * CS2))).prod(1)
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+@pytest.mark.parametrize("tau", [0.55, 0.8, 2.0, 5.0])
+def test_uniform_flow_equilibrium_is_fixed_point(oracle_mod, scheme, tau):
+    """Eq. flbe2 relaxes only the non-equilibrium part f - f^eq (Eqs. f^neq,
+    moments2): a uniform flow at its own equilibrium, f = f^eq(rho, u0), is
+    therefore a fixed point of collision and streaming for every tau when
+    kT = 0.  BGK- and GMF-FLBM use the second-order f^eq; Reg-FLBM its
+    full-order (product-form) equilibrium.  An a2neq taken as sum (f - w rho)
+    H2, the full second moment, relaxes rho u u as well and moves the state by
+    (1 - omega) rho u u ~ 1e-3 per step."""
+    T = oracle_mod.tables()
+    c, w = T["c"].astype(float), T["w"]
+    rho, u0 = 1.07, np.array([0.05, -0.03, 0.02])
+    feq = _feq_product_form(c, rho, u0) if scheme == 2 else _feq_second_order(c, w, rho, u0)
+    nx, ny, nz = 4, 3, 5
+    f0 = np.broadcast_to(feq[:, None, None, None], (27, nz, ny, nx)).copy()
+    box = oracle_mod.Box(nx, ny, nz, tau=tau, kT=0.0, scheme=scheme)
+    box.set_f(f0)
+    box.step(10)
+    assert np.abs(box.get_f() - f0).max() < 1e-14   # ten steps of roundoff on f ~ 0.3
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+@pytest.mark.parametrize("tau", [0.6, 2.0])
+def test_collision_relaxes_nonequilibrium_moments(oracle_mod, scheme, tau):
+    """Moments of the kT = 0 collision of a perturbed state moving at u ~ 0.06
+    (Eq. flbe2 and the f^eq / f^neq that follow it; Eq. flbe for BGK):
+    second moment Pi*_ab = rho u_a u_b + rho c_s^2 d_ab + (1 - omega) Pi^neq_ab
+    with Pi^neq = Pi - rho u u - rho c_s^2 d (the Galilean offset of Eq.
+    moments2: sum (f - f^eq) H2 = sum f H2 - rho u u); ghost coefficients
+    sum_i f*_i e_ki (e_k the tensor-product Hermite polynomial, built here):
+    (1 - omega) m_k for BGK (the second-order f^eq has none), 0 for GMF (the
+    filter), rho u^deg(k) for Reg (the Maxwellian's)."""
+    T = oracle_mod.tables()
+    c, w = T["c"].astype(float), T["w"]
+    u0 = np.array([0.06, -0.04, 0.03])
+    f = _feq_second_order(c, w, 1.0, u0) + 0.02 * w * inputs.normal_field(27, seed=31 + scheme)
+    rho = f.sum()
+    u = c.T @ f / rho
+    omega = 1.0 / tau
+    fs = oracle_mod.collide_node(scheme, tau, 0.0, f)
+    pi = np.einsum("i,ia,ib->ab", f, c, c)
+    pi_s = np.einsum("i,ia,ib->ab", fs, c, c)
+    pi_eq = rho * np.outer(u, u) + rho * CS2 * np.eye(3)
+    assert np.abs(pi_s - (pi_eq + (1 - omega) * (pi - pi_eq))).max() < 1e-15
+    assert np.abs(pi - pi_eq).max() > 1e-3            # a real non-equilibrium part
+    assert np.abs(rho * np.outer(u, u)).max() > 1e-3  # and a real rho u u
+    p = [lambda v: np.ones_like(v), lambda v: v, lambda v: v * v - CS2]
+    for a in range(3):
+        for b in range(3):
+            for g in range(3):
+                if a + b + g < 3 or max(a, b, g) > 2:
+                    continue
+                e = p[a](c[:, 0]) * p[b](c[:, 1]) * p[g](c[:, 2])
+                if scheme == 0:
+                    expect = (1 - omega) * (e @ f)
+                elif scheme == 1:
+                    expect = 0.0
+                else:
+                    expect = rho * u[0] ** a * u[1] ** b * u[2] ** g
+                assert abs(e @ fs - expect) < 1e-15, (scheme, a, b, g)
+
+
 def _rotate_state(f, c, perm, signs):
     """Apply the cube symmetry x'_a = signs[a] * x_{perm[a]} to a population
     field f[i, z, y, x] on a cubic periodic box."""
