@@ -86,7 +86,10 @@ def parse_args(argv=None):
     ap.add_argument("--tuning", type=int, nargs=4, default=None,
                     metavar=("ITEM_NODES", "STAGES", "WARPS", "CTAS_PER_SM"),
                     help="ensemble: this launch shape instead of the autotuner's")
-    return ap.parse_args(argv)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3 (untimed warm-up steps before the timed region)")
+    return args
 
 
 # ----------------------------------------------------------------------------
@@ -424,7 +427,9 @@ def run_ours(args, rank, local, ws):
                        stats_every=1, torch_memory=True, stream=stream,
                        state_form=flbm.FLBM_STATE_MOMENTS if moments else flbm.FLBM_STATE_POPULATIONS)
     lat.init_thermal(seed)           # invariant-measure start (library kernel)
-    lat.step(args.warmup)
+    lat.step(1)                      # first warm-up step: its reduction holds the start mass
+    mass0 = lat.stats()["mass"]
+    lat.step(args.warmup - 1)
     lat.stats_reset()
     props = torch.cuda.get_device_properties(dev)
     uuid = getattr(props, "uuid", None)
@@ -544,7 +549,13 @@ def run_ours(args, rank, local, ws):
             "equipartition": {"u2_avg_over_kT_rho0": u2_ratio,
                               "max_abs_error": max(abs(x - 1) for x in u2_ratio),
                               "er": st["er"], "samples": st["n_samples"]},
-            "mass_rel_drift": st["mass"] / (N * rho0) - 1.0,
+            # drift: the mass of the last reduced step against that of the
+            # thermal start (args.warmup - 1 + args.steps steps apart); the
+            # start's own offset from N rho0 is the sample's thermal spread
+            "mass": {"rel_drift": st["mass"] / mass0 - 1.0,
+                     "steps_apart": args.warmup - 1 + args.steps,
+                     "start_offset": mass0 / (N * rho0) - 1.0,
+                     "start_offset_sd": (3.0 * N * rho0 * kT) ** 0.5 / (N * rho0)},
         }
         print(json.dumps(line), flush=True)
     lat.close()

@@ -249,8 +249,13 @@ const char *flbm_last_error(const flbm_ctx *c);
  * device, or a host program that embeds the solver under a fixed memory
  * budget.  The paper has no counterpart; this is a deployment interface.
  *
- *   p          box, scheme, tau, kT, rho0, seed, noise_rho0; precision must be
- *              FLBM_FP32 (FLBM_E_UNSUPPORTED otherwise); stats_every ignored.
+ *   p          box, scheme, tau, kT, rho0, seed, noise_rho0, noise_stream,
+ *              checked as flbm_create checks them (FLBM_E_INVALID); precision
+ *              must be FLBM_FP32, state_form FLBM_STATE_POPULATIONS and the
+ *              scheme BGK, GMF or Reg (FLBM_E_UNSUPPORTED otherwise);
+ *              stats_every ignored.  The launch shape is flbm_create's for
+ *              the same box and environment (FLBM_ROWS, FLBM_CTAS_PER_SM), so
+ *              populations and sums equal those of flbm_step + flbm_stats.
  *   dev_state  27 N floats of deviations g_i = f_i - w_i rho0, SoA planes,
  *              256-byte aligned, updated in place (AA pattern).
  *   step       time index t of this collision (the noise counter).
@@ -266,8 +271,9 @@ const char *flbm_last_error(const flbm_ctx *c);
  * of 208 KiB that every GPU loading the library keeps until process exit;
  * a launch needing more than its 2048 CTA slots is rejected with
  * FLBM_E_INVALID.  The first call on a device resolves that array's address
- * (cudaGetSymbolAddress) with the device current; make it before any stream
- * capture.  Every call reuses the same array, so calls that overlap on the
+ * (cudaGetSymbolAddress) with the device current and keeps it; make it
+ * before any stream capture, and do not use the library on a device across
+ * a cudaDeviceReset.  Every call reuses the same array, so calls that overlap on the
  * GPU (other streams, other threads) race and must be serialised by the
  * caller.  Errors: FLBM_E_INVALID, FLBM_E_UNSUPPORTED, FLBM_E_CUDA,
  * FLBM_E_UNSTABLE, FLBM_E_TIMEOUT; text via flbm_last_error(NULL). */

@@ -360,29 +360,13 @@ int flbm::create_ctx(const flbm_params *p, void *dev_buf, size_t dev_bytes, void
         step_occupancy_f32(p->scheme, uint32_t(p->nx), c->n, true, occ, occ_rows);
     else
         step_occupancy_f16(p->scheme, uint32_t(p->nx), c->n, true, occ, occ_rows);
-    const uint64_t nchunks = uint64_t((p->nx + kBlock - 1) / kBlock) * p->ny * p->nz;
-    // FLBM_CTAS_PER_SM (environment) caps the direct kernel's grid below the
-    // occupancy limit; a tuning knob, the default is the occupancy limit
-    int per_sm = occ;
-    if (const char *env = std::getenv("FLBM_CTAS_PER_SM")) {
-        const int v = std::atoi(env);
-        if (v > 0 && v < occ) per_sm = v;
-    }
-    if (p->scheme == FLBM_LEARNED) per_sm = learned_occupancy(c->n);
-    c->grid = int(std::min<uint64_t>(nchunks, uint64_t(c->nsm) * per_sm));
-    if (c->grid < 1) c->grid = 1;
+    step_grids(*p, c->nsm, occ, occ_rows, c->grid, c->row_grid);
     // FLBM_INJECT_STARVE=1 (environment, failure-injection tests only): the
     // row pipeline expects 16 bytes more than it copies (the learned step
-    // never commits its first network layer), so the bounded waits run out
-    // and flbm_step reports FLBM_E_TIMEOUT
+    // issues no first-layer MMA), so the bounded waits run out and flbm_step
+    // reports FLBM_E_TIMEOUT
     if (const char *inj = std::getenv("FLBM_INJECT_STARVE"))
         if (std::atoi(inj) == 1) c->tx_pad = 16;
-    // FLBM_ROWS=0 (environment) disables the TMA row pipeline
-    const char *rows_env = std::getenv("FLBM_ROWS");
-    if (occ_rows > 0 && p->scheme != FLBM_LEARNED && !(rows_env && std::atoi(rows_env) == 0)) {
-        const uint64_t nrows = uint64_t(p->ny) * p->nz;
-        c->row_grid = int(std::min<uint64_t>(nrows, uint64_t(c->nsm) * occ_rows));
-    }
     if (p->state_form == FLBM_STATE_MOMENTS) {
         for (int b = 0; b < 2; ++b) {
             e = cudaMalloc(&c->ms[b], size_t(kMsVals) * c->n * sizeof(float));
@@ -411,6 +395,29 @@ int flbm::create_ctx(const flbm_params *p, void *dev_buf, size_t dev_bytes, void
 }
 
 namespace flbm {
+void step_grids(const flbm_params &p, int nsm, int occ, int occ_rows, int &grid, int &row_grid)
+{
+    const uint64_t n = uint64_t(p.nx) * uint64_t(p.ny) * uint64_t(p.nz);
+    const uint64_t nchunks = uint64_t((p.nx + kBlock - 1) / kBlock) * p.ny * p.nz;
+    // FLBM_CTAS_PER_SM (environment) caps the direct kernel's grid below the
+    // occupancy limit; a tuning knob, the default is the occupancy limit
+    int per_sm = occ;
+    if (const char *env = std::getenv("FLBM_CTAS_PER_SM")) {
+        const int v = std::atoi(env);
+        if (v > 0 && v < occ) per_sm = v;
+    }
+    if (p.scheme == FLBM_LEARNED) per_sm = learned_occupancy(n);
+    grid = int(std::min<uint64_t>(nchunks, uint64_t(nsm) * per_sm));
+    if (grid < 1) grid = 1;
+    // FLBM_ROWS=0 (environment) disables the TMA row pipeline
+    row_grid = 0;
+    const char *rows_env = std::getenv("FLBM_ROWS");
+    if (occ_rows > 0 && p.scheme != FLBM_LEARNED && !(rows_env && std::atoi(rows_env) == 0)) {
+        const uint64_t nrows = uint64_t(p.ny) * p.nz;
+        row_grid = int(std::min<uint64_t>(nrows, uint64_t(nsm) * occ_rows));
+    }
+}
+
 void fill_step_constants(const flbm_params &p, StepArgs<float> &a) { fill_constants_t<float>(p, a); }
 void fill_step_constants(const flbm_params &p, StepArgs<double> &a) { fill_constants_t<double>(p, a); }
 void set_thread_error(const char *msg) { g_create_error = msg; }

@@ -146,6 +146,10 @@ void step_occupancy_f16(int scheme, uint32_t nx, uint64_t n, bool stats, int &di
 // Step constants shared by flbm_step and flbm_step_noalloc (capi.cu): the
 // Philox round keys, the density used by the noise, and the per-mode
 // relaxation / equilibrium / noise coefficients of the scheme.
+// Grids of the direct step kernel and of the row pipeline (0: not used) for
+// a box on nsm SMs, given the kernels' resident CTAs per SM; honours the
+// FLBM_CTAS_PER_SM and FLBM_ROWS=0 environment knobs.
+void step_grids(const flbm_params &p, int nsm, int occ, int occ_rows, int &grid, int &row_grid);
 void fill_step_constants(const flbm_params &p, StepArgs<float> &a);
 void fill_step_constants(const flbm_params &p, StepArgs<double> &a);
 // Set the calling thread's error text returned by flbm_last_error(NULL).

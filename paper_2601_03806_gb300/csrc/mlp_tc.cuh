@@ -157,8 +157,9 @@ __device__ __forceinline__ void mlp_sync_for_mma(uint32_t q)
 // y = its 27 outputs.  work() runs while the first layer's MMAs are in flight.  Returns
 // false (on every thread) if a wait ran out; the MMAs are then drained with
 // one more bounded wait before returning.  starve (failure injection, tests
-// only): the first layer's completion is never committed, so the waits run
-// out.
+// only): the issuer issues none of the first layer's MMAs and commits
+// nothing, so the group's wait runs out with no tensor-core work in flight
+// when the tensor memory is later released.
 template <typename Work>
 __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const float (&x)[kMlpIn],
                                          float (&y)[kMlpOut], Work &&work, bool starve = false)
@@ -179,14 +180,14 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
         store_row16(a1p, kSbo32, t, 16, v);
     }
     mlp_sync_for_mma(q);
-    if (t == 0) {
+    if (t == 0 && !starve) {
         tc_fence_after();
         const uint32_t a1 = smem_u32(a1p);
 #pragma unroll
         for (uint32_t s = 0; s < 2; ++s)
             umma_bf16(tmem, umma_smem_desc(a1 + 256 * s, 128, kSbo32),
                       umma_smem_desc(w + kW1Off + 256 * s, 128, kSbo32), idesc64, s > 0);
-        if (!starve) umma_commit(&sm.bar[q]);
+        umma_commit(&sm.bar[q]);
     }
     work();
     bool ok = mlp_wait(sm, q, phase);
@@ -247,8 +248,9 @@ __device__ __forceinline__ bool mlp_tile(MlpSmem &sm, uint32_t &phase, const flo
         }
         return true;
     }
-    // a wait ran out: give the MMAs in flight one more bounded wait
-    mbar_wait(&sm.bar[q], phase);
+    // a wait ran out: give the MMAs in flight one more bounded wait (none
+    // are when starving)
+    if (!starve) mbar_wait(&sm.bar[q], phase);
     return false;
 }
 

@@ -13,8 +13,10 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <string>
 
 #include "../../include/flbm.h"
+#include "ctx.h"
 #include "internal.h"
 #include "lattice.cuh"
 
@@ -39,7 +41,9 @@ std::mutex g_setup_mutex;
 NoallocScratch *g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device (resolved once
-// per device, with that device current).
+// per device, with that device current, and kept: the library must not be
+// used on a device across a cudaDeviceReset, which unloads the module that
+// holds the array).
 cudaError_t scratch_address(int dev, NoallocScratch **out)
 {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
@@ -91,14 +95,18 @@ extern "C" int flbm_step_noalloc(const flbm_params *p, void *dev_state, int64_t 
                                  double *dev_sums, void *cuda_stream)
 {
     if (!p || !dev_state || !dev_sums) return noalloc_fail(FLBM_E_INVALID, "NULL argument");
-    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || !(p->tau > 0.5) || !(p->kT >= 0.0) ||
-        !(p->rho0 > 0.0) || p->scheme < FLBM_BGK || p->scheme > FLBM_REG || step < 0 ||
-        (parity != 0 && parity != 1) || (p->noise_rho0 != 0 && p->noise_rho0 != 1))
-        return noalloc_fail(FLBM_E_INVALID, "invalid parameters");
+    // every parameter check of flbm_create (box size, finite tau / kT / rho0,
+    // noise stream range, ...), then what this entry point adds
+    const std::string why = validate_params(p);
+    if (!why.empty()) return noalloc_fail(FLBM_E_INVALID, why.c_str());
+    if (step < 0 || (parity != 0 && parity != 1))
+        return noalloc_fail(FLBM_E_INVALID, "step must be >= 0 and parity 0 or 1");
     if (p->precision != FLBM_FP32)
         return noalloc_fail(FLBM_E_UNSUPPORTED, "flbm_step_noalloc serves FP32 storage only");
     if (p->state_form != FLBM_STATE_POPULATIONS)
         return noalloc_fail(FLBM_E_UNSUPPORTED, "flbm_step_noalloc steps population storage only");
+    if (p->scheme == FLBM_LEARNED)
+        return noalloc_fail(FLBM_E_UNSUPPORTED, "flbm_step_noalloc runs BGK-, GMF- or Reg-FLBM");
     if (reinterpret_cast<uintptr_t>(dev_state) % 256 != 0)
         return noalloc_fail(FLBM_E_INVALID, "dev_state must be 256-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -110,14 +118,14 @@ extern "C" int flbm_step_noalloc(const flbm_params *p, void *dev_state, int64_t 
     if (scratch_address(dev, &sc) != cudaSuccess)
         return noalloc_fail(FLBM_E_CUDA, "cudaGetSymbolAddress of the scratch array failed");
 
-    // the same launch shape flbm_step uses for this box
+    // the launch shape flbm_create picks for this box (step_grids, with the
+    // same environment knobs), so the populations and the order of the FP64
+    // sums are those of flbm_step + flbm_stats
     const uint64_t n = uint64_t(p->nx) * uint64_t(p->ny) * uint64_t(p->nz);
-    int occ = 1, occ_rows = 0;
-    step_occupancy_f32(p->scheme, uint32_t(p->nx), n, true, occ, occ_rows);
     const uint64_t nchunks = uint64_t((p->nx + kBlock - 1) / kBlock) * p->ny * p->nz;
-    const int grid = int(std::min<uint64_t>(nchunks, uint64_t(nsm) * occ));
-    int row_grid = 0;
-    if (occ_rows > 0) row_grid = int(std::min<uint64_t>(uint64_t(p->ny) * p->nz, uint64_t(nsm) * occ_rows));
+    int occ = 1, occ_rows = 0, grid = 0, row_grid = 0;
+    step_occupancy_f32(p->scheme, uint32_t(p->nx), n, true, occ, occ_rows);
+    step_grids(*p, nsm, occ, occ_rows, grid, row_grid);
     const int used = row_grid > 0 ? row_grid : grid;
     if (used > kNoallocMaxCtas)
         return noalloc_fail(FLBM_E_INVALID,

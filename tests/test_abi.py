@@ -77,6 +77,30 @@ def test_validation_before_device(F, kw, code):
     assert F.flbm_last_error(None)
 
 
+@pytest.mark.parametrize("kw,step,parity,code", [
+    (dict(noise_stream=1 << 24), 0, 0, -1), (dict(noise_stream=-1), 0, 0, -1),
+    (dict(tau=float("inf")), 0, 0, -1), (dict(kT=float("nan")), 0, 0, -1),
+    (dict(rho0=float("inf")), 0, 0, -1), (dict(nx=1 << 14, ny=1 << 14, nz=1 << 12), 0, 0, -1),
+    (dict(), -1, 0, -1), (dict(), 0, 2, -1),
+    (dict(precision=2), 0, 0, -6), (dict(precision=0), 0, 0, -6), (dict(scheme=3), 0, 0, -6),
+    (dict(state_form=1), 0, 0, -6),
+])
+def test_noalloc_validation_before_device(F, kw, step, parity, code):
+    """flbm_step_noalloc checks its parameters as flbm_create does (noise
+    stream range, finite tau / kT / rho0, box size) and rejects the storage
+    forms and schemes it does not serve, all before any CUDA call: the
+    pointers passed here are never dereferenced."""
+    args = dict(nx=8, ny=8, nz=8, tau=0.8, kT=1e-5, rho0=1.0, seed=1, scheme=1, precision=1,
+                noise_stream=0, state_form=0)
+    args.update(kw)
+    p = F.make_params(args["nx"], args["ny"], args["nz"], args["tau"], args["kT"], args["rho0"],
+                      args["seed"], args["scheme"], args["precision"], False, 1,
+                      noise_stream=args["noise_stream"], state_form=args["state_form"])
+    rc = F.flbm_step_noalloc(C.byref(p), C.c_void_p(256), step, parity, C.c_void_p(256), None)
+    assert rc == code
+    assert F.flbm_last_error(None)
+
+
 def test_state_bytes_and_params(F):
     p = F.make_params(512, 512, 512, 0.6, 1e-5)
     assert F.flbm_state_bytes(C.byref(p)) == 27 * 512 ** 3 * 4

@@ -91,7 +91,7 @@ def test_reference_arm_prints_the_contract_line():
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
+                          "--steps", "1", "--warmup", "3"], capture_output=True, text=True,
                          timeout=600, cwd=root, check=True).stdout
     lines = [ln for ln in out.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
