@@ -109,15 +109,19 @@ __host__ __device__ constexpr double b_of(int a, int b, int c)
 }
 
 // Scales of the kernel's transforms.  The forward pass returns
-// fwd_scale * M_abc (its degree-2 line sum is 2 s - o = 3 sum v p_2(c)); the
+// fwd_scale * M_abc: its degree-2 line sum is o - 2 s = -3 sum v p_2(c) (one
+// FMA with no negated operand), so each degree-2 axis contributes -3.  The
 // reconstruction consumes Q_abc = syn_scale * M_abc with syn_scale =
-// prod kappa(d), kappa = (1/6, 1/2, 1/2) = per-axis w1-prescale / beta, which
-// makes every 1-D synthesis pass (p0 - p1 + p2, 4 p0 - 2 p2, p0 + p1 + p2).
+// prod kappa(d), kappa = (4/6, 1/2, 1/2): per-axis w1-prescale / beta, times 4
+// on the degree-0 amplitude, which makes every 1-D synthesis pass
+// (t - p1, p0 - 2 p2, t + p1) with t = p0 / 4 + p2 (two FMAs and two adds;
+// the values at c = -1, 0, +1 of w1(c) (q0 + q1 c + q2 (c^2 - 1/3))).  Every
+// factor is exact in binary, so the scales change no rounding.
 __host__ __device__ constexpr double fwd_scale(int a, int b, int c)
 {
-    return (a == 2 ? 3.0 : 1.0) * (b == 2 ? 3.0 : 1.0) * (c == 2 ? 3.0 : 1.0);
+    return (a == 2 ? -3.0 : 1.0) * (b == 2 ? -3.0 : 1.0) * (c == 2 ? -3.0 : 1.0);
 }
-__host__ __device__ constexpr double kappa1d(int d) { return d == 0 ? 1.0 / 6.0 : 0.5; }
+__host__ __device__ constexpr double kappa1d(int d) { return d == 0 ? 2.0 / 3.0 : 0.5; }
 
 // sqrt(b_k / c_s^2) of mode (a,b,c): sqrt(3) prod sqrt(beta_d), with
 // sqrt(beta) = (1, 1/sqrt(3), sqrt(2)/3) written as literals so the product

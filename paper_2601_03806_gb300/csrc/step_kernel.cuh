@@ -89,38 +89,44 @@ template <> __device__ __forceinline__ float sqrt_<float>(float v) { return v * 
 // ---------------------------------------------------------------------------
 // 1-D transforms (see lattice.cuh for the scales)
 
+// Fused multiply-add of the arithmetic type (one rounding).
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Hermite analysis of a 3-point line (values at c = -1, 0, +1):
-// (sum v, sum v c, 3 sum v (c^2 - 1/3)); the factor 3 is undone through the
-// host-side mode coefficients (fwd_scale).
+// (sum v, sum v c, -3 sum v (c^2 - 1/3)); the factor -3 is undone through
+// the mode coefficients (fwd_scale).  Four operations: s = m + p,
+// d = p - m, h0 = s + o, h2 = o - 2 s (an FMA).
 template <typename R>
 __device__ __forceinline__ void analyse(R &m, R &o, R &p)
 {
     const R s = m + p;
     const R d = p - m;
     const R h0 = s + o;
-    const R h2 = R(2) * s - o;
+    const R h2 = fma_(s, R(-2), o);
     m = h0;
     o = d;
     p = h2;
 }
 
-// Synthesis of prescaled amplitudes (syn_scale): the values at c = -1, 0, +1
-// of w1(c) (q0 + q1 c + q2 (c^2 - 1/3)) for the unscaled q.
+// Synthesis of prescaled amplitudes (syn_scale, degree 0 carrying 4): the
+// values at c = -1, 0, +1 of w1(c) (q0 + q1 c + q2 (c^2 - 1/3)) for the
+// unscaled q.  t = p0 / 4 + p2 and p0 - 2 p2 are single FMAs whose exact
+// products make them equal to p0/4 + p2 and 4 (p0/4) - 2 p2 rounded once.
 template <typename R>
 __device__ __forceinline__ void synthesise(R &p0, R &p1, R &p2)
 {
-    const R t = p0 + p2;
-    const R z = R(4) * p0 - R(2) * p2;
+    const R t = fma_(p0, R(0.25), p2);
+    const R z = fma_(p2, R(-2), p0);
     p0 = t - p1;
     p2 = t + p1;
     p1 = z;
 }
 
 // The same two transforms on two lines at once (lines a and b).  In FP32
-// they run as packed FP32 pairs: five instructions for two lines instead of
-// eight or ten.  Each lane rounds exactly as the scalar code: p - m is
-// fma(m, -1, p), 2 s - o is fma(s, 2, -o) with -o exact, 4 p0 - 2 p2 is
-// fma(p0, 4, -2 p2) with -2 p2 exact, t - p1 is fma(p1, -1, t).
+// they run as packed FP32 pairs: four instructions for two lines instead of
+// eight.  Each lane rounds exactly as the scalar code (p - m is
+// fma(m, -1, p), t - p1 is fma(p1, -1, t)).
 template <typename R>
 __device__ __forceinline__ void analyse_pair(R &ma, R &mb, R &oa, R &ob, R &pa, R &pb)
 {
@@ -135,7 +141,7 @@ __device__ __forceinline__ void analyse_pair<float>(float &ma, float &mb, float 
     const float2 s = __fadd2_rn(m, p);
     const float2 d = __ffma2_rn(m, make_float2(-1.0f, -1.0f), p);
     const float2 h0 = __fadd2_rn(s, o);
-    const float2 h2 = __ffma2_rn(s, make_float2(2.0f, 2.0f), __fmul2_rn(o, make_float2(-1.0f, -1.0f)));
+    const float2 h2 = __ffma2_rn(s, make_float2(-2.0f, -2.0f), o);
     ma = h0.x;
     mb = h0.y;
     oa = d.x;
@@ -154,8 +160,8 @@ __device__ __forceinline__ void synthesise_pair<float>(float &p0a, float &p0b, f
                                                        float &p2a, float &p2b)
 {
     const float2 p0 = make_float2(p0a, p0b), p1 = make_float2(p1a, p1b), p2 = make_float2(p2a, p2b);
-    const float2 t = __fadd2_rn(p0, p2);
-    const float2 z = __ffma2_rn(p0, make_float2(4.0f, 4.0f), __fmul2_rn(p2, make_float2(-2.0f, -2.0f)));
+    const float2 t = __ffma2_rn(p0, make_float2(0.25f, 0.25f), p2);
+    const float2 z = __ffma2_rn(p2, make_float2(-2.0f, -2.0f), p0);
     const float2 r0 = __ffma2_rn(p1, make_float2(-1.0f, -1.0f), t);
     const float2 r2 = __fadd2_rn(t, p1);
     p0a = r0.x;
@@ -175,6 +181,74 @@ __device__ __forceinline__ R warp_sum(R v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Fused-reduction totals of a CTA, one slot per warp and sum (blockDim.x a
+// multiple of 32, at most 32 warps).  Threads add their nodes' terms in R;
+// every kFlushEvery rows (row pipeline) or chunks (direct kernel) each warp
+// adds its threads' partial sums (a warp_sum in R) to its slots and restarts
+// them, so that in FP32 no sum spans more than kFlushEvery rows of a
+// thread's nodes.  A slot is an unevaluated pair hi + lo kept by Knuth's
+// error-free TwoSum (no FP64 arithmetic in the loop: the FP64 pipe is slow),
+// and block_store_totals adds the slots in fixed warp order in FP64.
+constexpr int kFlushEvery = 8;
+
+template <typename R> struct TotSlot { R hi, lo; };
+
+// s + e = a + b exactly (round to nearest, no underflow).
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+__device__ __forceinline__ double two_sum(double a, double b, double &e)
+{
+    const double s = __dadd_rn(a, b);
+    const double bb = __dsub_rn(s, a);
+    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+    return s;
+}
+
+template <typename R>
+__device__ __forceinline__ void totals_init(TotSlot<R> (*tot)[NSTAT])
+{
+    for (int i = threadIdx.x; i < 32 * NSTAT; i += blockDim.x) tot[i / NSTAT][i % NSTAT] = TotSlot<R>{R(0), R(0)};
+}
+
+// All 32 lanes of the warp take part; lane s < NSTAT updates slot s.
+template <typename R>
+__device__ __forceinline__ void warp_flush(R (&acc)[NSTAT], TotSlot<R> (*tot)[NSTAT])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    R mine = R(0);
+#pragma unroll
+    for (int s = 0; s < NSTAT; ++s) {
+        const R v = warp_sum(acc[s]);
+        if (lane == s) mine = v;
+        acc[s] = R(0);
+    }
+    if (lane < NSTAT) {
+        TotSlot<R> t = tot[warp][lane];
+        R e;
+        t.hi = two_sum(t.hi, mine, e);
+        t.lo += e;
+        tot[warp][lane] = t;
+    }
+}
+
+// Every thread of the CTA calls this once, after its last warp_flush.
+template <typename R>
+__device__ __forceinline__ void block_store_totals(TotSlot<R> (*tot)[NSTAT], double *out)
+{
+    __syncthreads();
+    if (threadIdx.x < NSTAT) {
+        const int nw = blockDim.x >> 5;
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += double(tot[w][threadIdx.x].hi) + double(tot[w][threadIdx.x].lo);
+        out[threadIdx.x] = t;
+    }
 }
 
 // Per-CTA FP64 partials of the per-thread sums (blockDim.x a multiple of 32,
@@ -311,7 +385,8 @@ __device__ __forceinline__ void collide_modes(R (&v)[3][3][3], const A &a, R (&a
 
     if (STATS) {
         const R m2 = jx + jy + jz;
-        const R m3 = R(1.0 / 3.0) * (v[2][0][0] + v[0][2][0] + v[0][0][2]) + drho;
+        // the degree-2 projections carry fwd_scale -3
+        const R m3 = R(-1.0 / 3.0) * (v[2][0][0] + v[0][2][0] + v[0][0][2]) + drho;
         const R m4 = v[1][1][0] + v[1][0][1] + v[0][1][1];
         acc[S_DRHO] += drho;
         acc[S_JX] += jx;
@@ -482,11 +557,19 @@ struct Nbr {
 template <typename S, typename R, typename I, int SCHEME, bool ODD, bool STATS>
 __global__ void __launch_bounds__(kBlock, FLBM_MIN_BLOCKS) k_step(S *__restrict__ g, const StepArgs<R> a)
 {
+    __shared__ TotSlot<R> tot[32][NSTAT];
     R acc[NSTAT];
 #pragma unroll
     for (int s = 0; s < NSTAT; ++s) acc[s] = R(0);
+    if (STATS) {
+        totals_init(tot);
+        __syncthreads();
+    }
     const I N = I(a.n);
-    for (uint64_t ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x) {
+    uint32_t it = 0;
+    for (uint64_t ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x, ++it) {
+        // CTA-uniform: every thread walks the same chunks
+        if (STATS && it % kFlushEvery == kFlushEvery - 1) warp_flush(acc, tot);
         const uint32_t xc = uint32_t(ch % a.cpr);
         const uint64_t r = ch / a.cpr;
         const uint32_t y = uint32_t(r % a.ny);
@@ -523,7 +606,10 @@ __global__ void __launch_bounds__(kBlock, FLBM_MIN_BLOCKS) k_step(S *__restrict_
                     Conv<S, R>::st(g + idx, v[i][j][k]);
                 }
     }
-    if (STATS) block_reduce_store(acc, a.partials + size_t(blockIdx.x) * NSTAT);
+    if (STATS) {
+        warp_flush(acc, tot);
+        block_store_totals(tot, a.partials + size_t(blockIdx.x) * NSTAT);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -641,6 +727,7 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) <= 4 ? 2 : 1)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kRowStages], empty[kRowStages];
+    __shared__ TotSlot<R> tot[32][NSTAT];
     S *const stage = reinterpret_cast<S *>(smem_raw);
     const uint32_t nx = a.nx;
     const uint32_t nc = blockDim.x - 32;                  // compute threads
@@ -659,6 +746,7 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) <= 4 ? 2 : 1)
         }
         mbar_init_fence();
     }
+    if (STATS) totals_init(tot);
     __syncthreads();
 
     if (threadIdx.x >= nc) {
@@ -712,7 +800,8 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) <= 4 ? 2 : 1)
             // the first node's normals are drawn while the row's segments land
             R nz[kNoise];
             if (threadIdx.x < nx) draw_noise(a, rowbase + threadIdx.x, nz);
-            if (!mbar_wait(&full[s], uint32_t((k / kRowStages) & 1))) {
+            // the outcome is made warp-uniform: warp_flush needs every lane
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[s], uint32_t((k / kRowStages) & 1)))) {
                 if (lane == 0) atomicOr(a.flag, 2u);
                 break;
             }
@@ -746,9 +835,13 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) <= 4 ? 2 : 1)
             fence_proxy_async_smem();   // generic-proxy writes before the bulk store reads
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
+            if (STATS && k % kFlushEvery == kFlushEvery - 1) warp_flush(acc, tot);
         }
     }
-    if (STATS) block_reduce_store(acc, a.partials + size_t(blockIdx.x) * NSTAT);
+    if (STATS) {
+        warp_flush(acc, tot);
+        block_store_totals(tot, a.partials + size_t(blockIdx.x) * NSTAT);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -19,9 +19,11 @@ FP16 deviations g_i = f_i - w_i rho0 are read exactly):
 * u_a = j_a (1/rho) with rho = rho0 + drho (one rounding) and the hardware
   reciprocal (within 2 ulp): |du| <= (E + |u| (E + u rho)) / rho + 6 u |u|,
   and u_a^2 as a square;
-* accumulation: every thread adds its nodes' terms in FP32 (at most m per
-  thread), warps add 32 threads' sums in five FP32 levels, blocks and the
-  grid add in FP64: gamma(m + 6) sum_n (|x_n| + e_n), gamma(k) = k u / (1 - k u).
+* accumulation: every thread adds its nodes' terms in FP32, at most m of
+  them before its warp adds the 32 threads' sums in five FP32 levels into an
+  FP64 total (every 8 rows of the row pipeline, every 8 chunks of the direct
+  kernel); blocks and the grid add in FP64:
+  gamma(m + 6) sum_n (|x_n| + e_n), gamma(k) = k u / (1 - k u).
 The bound is sum_n e_n + gamma(m + 6) sum_n (|x_n| + e_n).
 """
 import numpy as np
@@ -72,16 +74,20 @@ def sums_and_bounds(oracle_mod, f, rho0, m_per_thread):
     return x.sum(1), e.sum(1) + g * (np.abs(x) + e).sum(1)
 
 
+FLUSH_EVERY = 8
+
+
 def nodes_per_thread_bound(nx, ny, nz):
-    """Nodes any thread of the step kernels adds at most, for a GB300's 152
-    SMs: the row pipeline gives each CTA ceil(rows / grid) rows and each
-    thread ceil(nx / 256) nodes of a row; the direct kernel one node per
-    128-node chunk, ceil(chunks / grid) chunks; both grids hold at least
-    min(work, 152) CTAs."""
+    """Nodes any thread of the step kernels adds in FP32 at most before its
+    warp folds the sums into FP64, for a GB300's 152 SMs: the row pipeline
+    gives each CTA ceil(rows / grid) rows, each thread ceil(nx / 256) nodes
+    of a row, and flushes every 8 rows; the direct kernel one node per
+    128-node chunk, ceil(chunks / grid) chunks, flushed every 8 chunks; both
+    grids hold at least min(work, 152) CTAs."""
     rows = ny * nz
     chunks = -(-nx // 128) * rows
-    row_kernel = -(-rows // min(rows, 152)) * -(-nx // 256)
-    direct = -(-chunks // min(chunks, 152))
+    row_kernel = min(-(-rows // min(rows, 152)), FLUSH_EVERY) * -(-nx // 256)
+    direct = min(-(-chunks // min(chunks, 152)), FLUSH_EVERY)
     return max(row_kernel, direct)
 
 

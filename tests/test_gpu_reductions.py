@@ -65,8 +65,8 @@ def test_reductions_match_oracle_sums(F, oracle_mod, precision, shape):
 @pytest.mark.parametrize("precision", [1, 2])
 def test_reductions_match_oracle_sums_256cube(F, oracle_mod, precision):
     """A 256^3 box (16.7 M nodes; the row pipeline gives each thread one node
-    of about 216 rows per step): one reduced step against the oracle's FP64
-    sums."""
+    of about 216 rows per step, folded into FP64 every 8 rows): one reduced
+    step against the oracle's FP64 sums."""
     n, rho0, kT = 256, 1.0, 1e-5
     g = F.Lattice(n, n, n, 0.6, kT, rho0=rho0, seed=3, precision=precision, stats_every=1)
     g.init_thermal(11)
