@@ -291,9 +291,9 @@ void flbm_destroy(flbm_ctx *c);
  * statistics need (Sec. III measures <u^2> and S(k) as averages).  The
  * paper runs one box at a time; the ensemble is this library's.  Every
  * replica evolves as the single box of the same flbm_params would (the same
- * noise; equal to the rounding of the storage type, as the two kernels fuse
- * multiply-adds differently), and the results do not depend on the launch
- * shape or on whether steps replay from the CUDA graph (bit for bit).
+ * noise and the same populations, bit for bit), and the results do not
+ * depend on the launch shape or on whether steps replay from the CUDA graph
+ * (bit for bit).
  *
  * Work decomposition: replica r is cut into items of whole x-rows of one
  * z-plane (about item_nodes nodes); all items of all replicas are split into

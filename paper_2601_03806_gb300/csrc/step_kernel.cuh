@@ -42,6 +42,7 @@
 
 #include <cuda_fp16.h>
 
+#include <cstdlib>
 #include <type_traits>
 
 #include "internal.h"
@@ -77,33 +78,67 @@ template <> __device__ __forceinline__ __half stage_st<__half>(float v) { return
 template <typename S> __device__ __forceinline__ S stage_st(double v);
 template <> __device__ __forceinline__ double stage_st<double>(double v) { return v; }
 
+// ---------------------------------------------------------------------------
+// Lane arithmetic.  A thread collides one node in V = float or double, or
+// two nodes in V = float2, one per lane, as Blackwell's packed FP32
+// instructions (FADD2 / FMUL2 / FFMA2: one instruction for both nodes).
+// Every operation below is one IEEE operation rounded once (no contraction
+// left to the compiler), so a float2 lane computes bit for bit what the
+// float code computes for that node.
+
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double vadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double vsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double vmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as fma(b, -1, a): the product is exact, so one rounding of a - b
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Scalar of the lane type's precision, one copy per lane.
+template <typename V> struct Lane { using T = V; };
+template <> struct Lane<float2> { using T = float; };
+template <typename V> __device__ __forceinline__ V vset(double c) { return V(c); }
+template <> __device__ __forceinline__ float2 vset<float2>(double c) { return make_float2(float(c), float(c)); }
+__device__ __forceinline__ float vbc(float c, float) { return c; }
+__device__ __forceinline__ double vbc(double c, double) { return c; }
+__device__ __forceinline__ float2 vbc(float c, float2) { return make_float2(c, c); }
+
 // Reciprocal and square root of the density: IEEE in FP64, the hardware
-// approximations (relative error ~1e-7) in FP32.
-template <typename R> __device__ __forceinline__ R rcp_(R v);
-template <> __device__ __forceinline__ double rcp_<double>(double v) { return 1.0 / v; }
-template <> __device__ __forceinline__ float rcp_<float>(float v) { return __fdividef(1.0f, v); }
-template <typename R> __device__ __forceinline__ R sqrt_(R v);
-template <> __device__ __forceinline__ double sqrt_<double>(double v) { return sqrt(v); }
-template <> __device__ __forceinline__ float sqrt_<float>(float v) { return v * rsqrtf(v); }
+// approximations (relative error ~1e-7) in FP32, per lane.
+__device__ __forceinline__ double rcp_(double v) { return 1.0 / v; }
+__device__ __forceinline__ float rcp_(float v) { return __fdividef(1.0f, v); }
+__device__ __forceinline__ float2 rcp_(float2 v) { return make_float2(rcp_(v.x), rcp_(v.y)); }
+__device__ __forceinline__ double sqrt_(double v) { return sqrt(v); }
+__device__ __forceinline__ float sqrt_(float v) { return __fmul_rn(v, rsqrtf(v)); }
+__device__ __forceinline__ float2 sqrt_(float2 v)
+{
+    return vmul(v, make_float2(rsqrtf(v.x), rsqrtf(v.y)));
+}
+// Whether any lane's density fails rho > 0 and rho finite.
+__device__ __forceinline__ bool bad_density(float r) { return !(r > 0.0f) || !(r < INFINITY); }
+__device__ __forceinline__ bool bad_density(double r) { return !(r > 0.0) || !(r < INFINITY); }
+__device__ __forceinline__ bool bad_density(float2 r) { return bad_density(r.x) || bad_density(r.y); }
 
 // ---------------------------------------------------------------------------
 // 1-D transforms (see lattice.cuh for the scales)
-
-// Fused multiply-add of the arithmetic type (one rounding).
-__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Hermite analysis of a 3-point line (values at c = -1, 0, +1):
 // (sum v, sum v c, -3 sum v (c^2 - 1/3)); the factor -3 is undone through
 // the mode coefficients (fwd_scale).  Four operations: s = m + p,
 // d = p - m, h0 = s + o, h2 = o - 2 s (an FMA).
-template <typename R>
-__device__ __forceinline__ void analyse(R &m, R &o, R &p)
+template <typename V>
+__device__ __forceinline__ void analyse(V &m, V &o, V &p)
 {
-    const R s = m + p;
-    const R d = p - m;
-    const R h0 = s + o;
-    const R h2 = fma_(s, R(-2), o);
+    const V s = vadd(m, p);
+    const V d = vsub(p, m);
+    const V h0 = vadd(s, o);
+    const V h2 = vfma(s, vset<V>(-2.0), o);
     m = h0;
     o = d;
     p = h2;
@@ -113,22 +148,21 @@ __device__ __forceinline__ void analyse(R &m, R &o, R &p)
 // values at c = -1, 0, +1 of w1(c) (q0 + q1 c + q2 (c^2 - 1/3)) for the
 // unscaled q.  t = p0 / 4 + p2 and p0 - 2 p2 are single FMAs whose exact
 // products make them equal to p0/4 + p2 and 4 (p0/4) - 2 p2 rounded once.
-template <typename R>
-__device__ __forceinline__ void synthesise(R &p0, R &p1, R &p2)
+template <typename V>
+__device__ __forceinline__ void synthesise(V &p0, V &p1, V &p2)
 {
-    const R t = fma_(p0, R(0.25), p2);
-    const R z = fma_(p2, R(-2), p0);
-    p0 = t - p1;
-    p2 = t + p1;
+    const V t = vfma(p0, vset<V>(0.25), p2);
+    const V z = vfma(p2, vset<V>(-2.0), p0);
+    p0 = vsub(t, p1);
+    p2 = vadd(t, p1);
     p1 = z;
 }
 
-// The same two transforms on two lines at once (lines a and b).  In FP32
-// they run as packed FP32 pairs: four instructions for two lines instead of
-// eight.  Each lane rounds exactly as the scalar code (p - m is
-// fma(m, -1, p), t - p1 is fma(p1, -1, t)).
-template <typename R>
-__device__ __forceinline__ void analyse_pair(R &ma, R &mb, R &oa, R &ob, R &pa, R &pb)
+// The same two transforms on two lines of one node at once (lines a and
+// b).  In FP32 they run as packed FP32 pairs: four instructions for two
+// lines instead of eight, each lane rounded exactly as the scalar code.
+template <typename V>
+__device__ __forceinline__ void analyse_pair(V &ma, V &mb, V &oa, V &ob, V &pa, V &pb)
 {
     analyse(ma, oa, pa);
     analyse(mb, ob, pb);
@@ -137,20 +171,17 @@ template <>
 __device__ __forceinline__ void analyse_pair<float>(float &ma, float &mb, float &oa, float &ob, float &pa,
                                                     float &pb)
 {
-    const float2 m = make_float2(ma, mb), o = make_float2(oa, ob), p = make_float2(pa, pb);
-    const float2 s = __fadd2_rn(m, p);
-    const float2 d = __ffma2_rn(m, make_float2(-1.0f, -1.0f), p);
-    const float2 h0 = __fadd2_rn(s, o);
-    const float2 h2 = __ffma2_rn(s, make_float2(-2.0f, -2.0f), o);
-    ma = h0.x;
-    mb = h0.y;
-    oa = d.x;
-    ob = d.y;
-    pa = h2.x;
-    pb = h2.y;
+    float2 m = make_float2(ma, mb), o = make_float2(oa, ob), p = make_float2(pa, pb);
+    analyse(m, o, p);
+    ma = m.x;
+    mb = m.y;
+    oa = o.x;
+    ob = o.y;
+    pa = p.x;
+    pb = p.y;
 }
-template <typename R>
-__device__ __forceinline__ void synthesise_pair(R &p0a, R &p0b, R &p1a, R &p1b, R &p2a, R &p2b)
+template <typename V>
+__device__ __forceinline__ void synthesise_pair(V &p0a, V &p0b, V &p1a, V &p1b, V &p2a, V &p2b)
 {
     synthesise(p0a, p1a, p2a);
     synthesise(p0b, p1b, p2b);
@@ -159,17 +190,14 @@ template <>
 __device__ __forceinline__ void synthesise_pair<float>(float &p0a, float &p0b, float &p1a, float &p1b,
                                                        float &p2a, float &p2b)
 {
-    const float2 p0 = make_float2(p0a, p0b), p1 = make_float2(p1a, p1b), p2 = make_float2(p2a, p2b);
-    const float2 t = __ffma2_rn(p0, make_float2(0.25f, 0.25f), p2);
-    const float2 z = __ffma2_rn(p2, make_float2(-2.0f, -2.0f), p0);
-    const float2 r0 = __ffma2_rn(p1, make_float2(-1.0f, -1.0f), t);
-    const float2 r2 = __fadd2_rn(t, p1);
-    p0a = r0.x;
-    p0b = r0.y;
-    p1a = z.x;
-    p1b = z.y;
-    p2a = r2.x;
-    p2b = r2.y;
+    float2 p0 = make_float2(p0a, p0b), p1 = make_float2(p1a, p1b), p2 = make_float2(p2a, p2b);
+    synthesise(p0, p1, p2);
+    p0a = p0.x;
+    p0b = p0.y;
+    p1a = p1.x;
+    p1b = p1.y;
+    p2a = p2.x;
+    p2b = p2.y;
 }
 
 // ---------------------------------------------------------------------------
@@ -217,17 +245,22 @@ __device__ __forceinline__ void totals_init(TotSlot<R> (*tot)[NSTAT])
     for (int i = threadIdx.x; i < 32 * NSTAT; i += blockDim.x) tot[i / NSTAT][i % NSTAT] = TotSlot<R>{R(0), R(0)};
 }
 
+// A thread's partial sum of both lanes.
+__device__ __forceinline__ float lane_total(float v) { return v; }
+__device__ __forceinline__ double lane_total(double v) { return v; }
+__device__ __forceinline__ float lane_total(float2 v) { return __fadd_rn(v.x, v.y); }
+
 // All 32 lanes of the warp take part; lane s < NSTAT updates slot s.
-template <typename R>
-__device__ __forceinline__ void warp_flush(R (&acc)[NSTAT], TotSlot<R> (*tot)[NSTAT])
+template <typename V, typename R>
+__device__ __forceinline__ void warp_flush(V (&acc)[NSTAT], TotSlot<R> (*tot)[NSTAT])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     R mine = R(0);
 #pragma unroll
     for (int s = 0; s < NSTAT; ++s) {
-        const R v = warp_sum(acc[s]);
+        const R v = warp_sum(lane_total(acc[s]));
         if (lane == s) mine = v;
-        acc[s] = R(0);
+        acc[s] = vset<V>(0.0);
     }
     if (lane < NSTAT) {
         TotSlot<R> t = tot[warp][lane];
@@ -275,8 +308,8 @@ __device__ __forceinline__ void block_reduce_store(const R (&acc)[NSTAT], double
 // a6, first half: the node's 23 standard normals r_k (k = 4..26), drawn from
 // Philox4x32-10 keyed on (seed; node, step, block) + Box-Muller and scaled by
 // the compile-time syn_scale_k sqrt(b_k / c_s^2): nz[k - 4].  They depend
-// only on (node, step), so the kernels draw them while the populations are
-// still in flight.
+// only on (node, step), so the kernels can draw them while the populations
+// are still in flight.
 
 constexpr int kNoise = kQ - 4;
 
@@ -290,27 +323,90 @@ __device__ __forceinline__ u32x4 noise_block(const StepArgs<R> &a, uint32_t node
     return philox4x32_10_r2(node, a.ph_zk, a.ph_u1[blk], a.ph_u2[blk], a.ph_u3[blk], a.rk);
 }
 
+// Box-Muller (1958) on the uniforms of words (w1, w2), returned as a
+// radius rad = sqrt(-2 ln u1) >= 0 and (ca, sa) = -(cos, sin)(2 pi u2): the
+// standard normals are -rad ca and -rad sa, and the sign is folded into the
+// mode scale (noise_scale).  FP32: hardware log2 (absolute error <= 2^-22
+// on [0.5, 1), <= 2 ulp below), so the radius has absolute error <= ln2
+// 2^-22 / rad (~1.7e-7 / rad: below 1e-6 for u1 <= 0.986, 98.6 % of draws,
+// at most 4.7e-4 at the smallest radius 3.5e-4, u1 = 1 - 2^-24); the angle
+// is taken as 2 pi u2 - pi in (-pi, pi), where the hardware sin/cos hold
+// their 2^-21.4 absolute error bound.
+__device__ __forceinline__ void normal_pair(uint32_t w1, uint32_t w2, float &rad, float &ca, float &sa)
+{
+    const float u1 = uniform23f(w1);
+    const float u2 = uniform23f(w2);
+    const float t = __fmul_rn(-1.3862943611198906f, __log2f(u1));   // -2 ln u1
+    rad = __fmul_rn(t, rsqrtf(t));
+    __sincosf(__fmaf_rn(u2, 6.2831853071795865f, -3.1415926535897932f), &sa, &ca);
+}
+__device__ __forceinline__ void normal_pair(uint32_t w1, uint32_t w2, double &rad, double &ca, double &sa)
+{
+    const double u1 = uniform23d(w1);
+    const double u2 = uniform23d(w2);
+    rad = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    ca = -c;
+    sa = -s;
+}
+// Two nodes, one per lane (words of node a in .x, of node b in .y).
+__device__ __forceinline__ void normal_pair(uint2 w1, uint2 w2, float2 &rad, float2 &ca, float2 &sa)
+{
+    const float2 c1 = make_float2(-(1.0f - 0x1p-24f), -(1.0f - 0x1p-24f));
+    const float2 u1 = __fadd2_rn(make_float2(__uint_as_float(0x3f800000u | (w1.x >> 9)),
+                                             __uint_as_float(0x3f800000u | (w1.y >> 9))), c1);
+    const float2 u2 = __fadd2_rn(make_float2(__uint_as_float(0x3f800000u | (w2.x >> 9)),
+                                             __uint_as_float(0x3f800000u | (w2.y >> 9))), c1);
+    const float2 t = __fmul2_rn(make_float2(-1.3862943611198906f, -1.3862943611198906f),
+                                make_float2(__log2f(u1.x), __log2f(u1.y)));
+    rad = __fmul2_rn(t, make_float2(rsqrtf(t.x), rsqrtf(t.y)));
+    const float2 ang = __ffma2_rn(u2, make_float2(6.2831853071795865f, 6.2831853071795865f),
+                                  make_float2(-3.1415926535897932f, -3.1415926535897932f));
+    __sincosf(ang.x, &sa.x, &ca.x);
+    __sincosf(ang.y, &sa.y, &ca.y);
+}
+
+// The four normals of Philox block blk as (rad0, c0, s0, rad1, c1, s1):
+// r_{4+4 blk + m} = -(rad0 c0, rad0 s0, rad1 c1, rad1 s1)[m].  V = float2:
+// nodes node and node + 1.
+template <typename V, typename A>
+__device__ __forceinline__ void block_normals(const A &a, uint32_t node, int blk, V &rad0, V &c0, V &s0, V &rad1,
+                                              V &c1, V &s1)
+{
+    if constexpr (std::is_same<V, float2>::value) {
+        const u32x4 oa = noise_block(a, node, blk), ob = noise_block(a, node + 1, blk);
+        normal_pair(make_uint2(oa.x, ob.x), make_uint2(oa.y, ob.y), rad0, c0, s0);
+        normal_pair(make_uint2(oa.z, ob.z), make_uint2(oa.w, ob.w), rad1, c1, s1);
+    } else {
+        const u32x4 o = noise_block(a, node, blk);
+        normal_pair(o.x, o.y, rad0, c0, s0);
+        normal_pair(o.z, o.w, rad1, c1, s1);
+    }
+}
+
+// Scale of mode mk's normal in the reconstruction's units: syn_scale
+// sqrt(b_k / c_s^2), negated (normal_pair returns -r / rad).
+__host__ __device__ constexpr double noise_scale(int mk)
+{
+    return -syn_scale(mode_deg(mk) % 3, (mode_deg(mk) / 3) % 3, mode_deg(mk) / 9) *
+           sqrt_b_over_cs2(mode_deg(mk) % 3, (mode_deg(mk) / 3) % 3, mode_deg(mk) / 9);
+}
+
 // A is the step's scalar set: StepArgs<R> for one box, or a per-replica view
 // with the same member names (rk, step, ctr2, rho0, ...) for an ensemble.
-template <typename R, typename A>
-__device__ __forceinline__ void draw_noise(const A &a, uint32_t node, R (&nz)[kNoise])
+template <typename V, typename A>
+__device__ __forceinline__ void draw_noise(const A &a, uint32_t node, V (&nz)[kNoise])
 {
 #pragma unroll
     for (int blk = 0; blk < 6; ++blk) {
-        const u32x4 o = noise_block(a, node, blk);
-        R rad0, c0, s0, rad1, c1, s1;
-        box_muller(o.x, o.y, rad0, c0, s0);
-        box_muller(o.z, o.w, rad1, c1, s1);
-        const R trig[4] = {c0, s0, c1, s1};
+        V rad0, c0, s0, rad1, c1, s1;
+        block_normals(a, node, blk, rad0, c0, s0, rad1, c1, s1);
+        const V trig[4] = {c0, s0, c1, s1};
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int mk = 4 + 4 * blk + m;
-            if (mk < kQ) {
-                const int d = mode_deg(mk);
-                const int di = d % 3, dj = (d / 3) % 3, dk = d / 9;
-                const R kk = R(syn_scale(di, dj, dk) * sqrt_b_over_cs2(di, dj, dk));
-                nz[mk - 4] = ((m < 2 ? rad0 : rad1) * kk) * trig[m];
-            }
+            if (mk < kQ) nz[mk - 4] = vmul(vmul(m < 2 ? rad0 : rad1, vset<V>(noise_scale(mk))), trig[m]);
         }
     }
 }
@@ -318,16 +414,16 @@ __device__ __forceinline__ void draw_noise(const A &a, uint32_t node, R (&nz)[kN
 // ---------------------------------------------------------------------------
 // Maxwell-Boltzmann coefficient rho u_x^i u_y^j u_z^k of mode (i, j, k),
 // order >= 1, as j_first * (the remaining u factors).
-template <typename R>
-__device__ __forceinline__ R aeq_coef(int i, int j, int k, const R (&jj)[3], const R (&uu)[3])
+template <typename V>
+__device__ __forceinline__ V aeq_coef(int i, int j, int k, const V (&jj)[3], const V (&uu)[3])
 {
     const int first = i ? 0 : (j ? 1 : 2);
-    R aeq = jj[first];
+    V aeq = jj[first];
     const int rest[3] = {i - (first == 0), j - (first == 1), k - (first == 2)};
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax)
 #pragma unroll
-        for (int e = 0; e < rest[ax]; ++e) aeq *= uu[ax];
+        for (int e = 0; e < rest[ax]; ++e) aeq = vmul(aeq, uu[ax]);
     return aeq;
 }
 
@@ -341,13 +437,15 @@ __device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(
 // instability check, the fused reductions, and the deterministic
 // post-collision amplitudes qm in the reconstruction's units, Q = syn_scale
 // * M (noise not yet added); rho is the node's density, dj = (rho - rho0,
-// j_x, j_y, j_z) as projected.  PAIRS: the x and y passes take the lines
-// k = 0 and k = 2 as pairs (packed FP32 in FP32; the same bits either way,
-// the faster choice depends on the kernel's register budget).
-template <typename R, int SCHEME, bool STATS, bool PAIRS = true, typename A>
-__device__ __forceinline__ void collide_modes(R (&v)[3][3][3], const A &a, R (&acc)[NSTAT], R (&qm)[3][3][3],
-                                              R &rho, R (&dj)[4])
+// j_x, j_y, j_z) as projected.  V = float2 collides two nodes, one per lane.
+// PAIRS (V = float): the x and y passes take the lines k = 0 and k = 2 as
+// packed pairs (the same bits either way; the faster choice depends on the
+// kernel's register budget).
+template <typename V, int SCHEME, bool STATS, bool PAIRS = true, typename A>
+__device__ __forceinline__ void collide_modes(V (&v)[3][3][3], const A &a, V (&acc)[NSTAT], V (&qm)[3][3][3],
+                                              V &rho, V (&dj)[4])
 {
+    using T = typename Lane<V>::T;
     // a2: forward Hermite projection, three 1-D passes
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -372,41 +470,42 @@ __device__ __forceinline__ void collide_modes(R (&v)[3][3][3], const A &a, R (&a
 #pragma unroll
         for (int j = 0; j < 3; ++j) analyse(v[i][j][0], v[i][j][1], v[i][j][2]);
 
-    const R drho = v[0][0][0];
-    rho = a.rho0 + drho;
-    const R jx = v[1][0][0], jy = v[0][1][0], jz = v[0][0][1];
-    const R irho = rcp_(rho);
-    const R ux = jx * irho, uy = jy * irho, uz = jz * irho;
+    const V drho = v[0][0][0];
+    rho = vadd(vbc(a.rho0, drho), drho);
+    const V jx = v[1][0][0], jy = v[0][1][0], jz = v[0][0][1];
+    const V irho = rcp_(rho);
+    const V ux = vmul(jx, irho), uy = vmul(jy, irho), uz = vmul(jz, irho);
 
-    if (!(rho > R(0)) || !(rho < R(INFINITY))) {
+    if (bad_density(rho)) {
         atomicOr(a.flag, 1u);
         atomicMin(a.bad_step, (unsigned long long)a.step);
     }
 
     if (STATS) {
-        const R m2 = jx + jy + jz;
         // the degree-2 projections carry fwd_scale -3
-        const R m3 = R(-1.0 / 3.0) * (v[2][0][0] + v[0][2][0] + v[0][0][2]) + drho;
-        const R m4 = v[1][1][0] + v[1][0][1] + v[0][1][1];
-        acc[S_DRHO] += drho;
-        acc[S_JX] += jx;
-        acc[S_JY] += jy;
-        acc[S_JZ] += jz;
-        acc[S_UX2] += ux * ux;
-        acc[S_UY2] += uy * uy;
-        acc[S_UZ2] += uz * uz;
-        acc[S_M3] += m3;
-        acc[S_M4] += m4;
-        acc[S_M1SQ] += drho * drho;
-        acc[S_M2SQ] += m2 * m2;
-        acc[S_M3SQ] += m3 * m3;
-        acc[S_M4SQ] += m4 * m4;
+        const V m2 = vadd(vadd(jx, jy), jz);
+        const V m3 = vfma(vset<V>(-1.0 / 3.0), vadd(vadd(v[2][0][0], v[0][2][0]), v[0][0][2]), drho);
+        const V m4 = vadd(vadd(v[1][1][0], v[1][0][1]), v[0][1][1]);
+        acc[S_DRHO] = vadd(acc[S_DRHO], drho);
+        acc[S_JX] = vadd(acc[S_JX], jx);
+        acc[S_JY] = vadd(acc[S_JY], jy);
+        acc[S_JZ] = vadd(acc[S_JZ], jz);
+        acc[S_UX2] = vfma(ux, ux, acc[S_UX2]);
+        acc[S_UY2] = vfma(uy, uy, acc[S_UY2]);
+        acc[S_UZ2] = vfma(uz, uz, acc[S_UZ2]);
+        acc[S_M3] = vadd(acc[S_M3], m3);
+        acc[S_M4] = vadd(acc[S_M4], m4);
+        acc[S_M1SQ] = vfma(drho, drho, acc[S_M1SQ]);
+        acc[S_M2SQ] = vfma(m2, m2, acc[S_M2SQ]);
+        acc[S_M3SQ] = vfma(m3, m3, acc[S_M3SQ]);
+        acc[S_M4SQ] = vfma(m4, m4, acc[S_M4SQ]);
     }
 
     // a3-a5: post-collision amplitudes in the reconstruction's units,
     // Q = syn_scale * M.  The pre-collision moments v carry fwd_scale.
-    const R jj[3] = {jx, jy, jz};
-    const R uu[3] = {ux, uy, uz};
+    const V jj[3] = {jx, jy, jz};
+    const V uu[3] = {ux, uy, uz};
+    const V lam = vbc(a.lambda, drho), om = vbc(a.omega, drho);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -414,23 +513,23 @@ __device__ __forceinline__ void collide_modes(R (&v)[3][3][3], const A &a, R (&a
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const int ord = mode_order(i, j, k);
-                const R syn = R(syn_scale(i, j, k));
-                const R unfwd = R(1.0 / fwd_scale(i, j, k));
-                R q;
+                const V syn = vset<V>(syn_scale(i, j, k));
+                const V unfwd = vset<V>(1.0 / fwd_scale(i, j, k));
+                V q;
                 if (ord == 0) {
-                    q = drho * syn;                             // deviation of M_0 = rho
+                    q = vmul(drho, syn);                        // deviation of M_0 = rho
                 } else if (ord == 1) {
-                    q = v[i][j][k] * syn;                       // momentum, conserved
+                    q = vmul(v[i][j][k], syn);                  // momentum, conserved
                 } else if (ord == 2 || SCHEME == 2) {
-                    const R aeq = aeq_coef(i, j, k, jj, uu);
+                    const V aeq = aeq_coef(i, j, k, jj, uu);
                     if (ord == 2)   // a_eq + (1 - omega)(m - a_eq) = omega a_eq + lambda m
-                        q = mul_rn(syn, a.lambda * (v[i][j][k] * unfwd) + a.omega * aeq);
+                        q = vmul(syn, vfma(lam, vmul(v[i][j][k], unfwd), vmul(om, aeq)));
                     else            // Reg ghosts: a_eq (unit relaxation)
-                        q = mul_rn(syn, aeq);
-                } else if (SCHEME == 0) {
-                    q = (syn * unfwd) * (a.lambda * v[i][j][k]);   // BGK ghosts
+                        q = vmul(syn, aeq);
+                } else if (SCHEME == 0) {                       // BGK ghosts
+                    q = vmul(vset<V>(T(syn_scale(i, j, k)) * T(1.0 / fwd_scale(i, j, k))), vmul(lam, v[i][j][k]));
                 } else {
-                    q = R(0);                                      // GMF: filtered
+                    q = vset<V>(0.0);                           // GMF: filtered
                 }
                 qm[i][j][k] = q;
             }
@@ -442,40 +541,38 @@ __device__ __forceinline__ void collide_modes(R (&v)[3][3][3], const A &a, R (&a
 
 // a6-a7: the node's noise added to the amplitudes qm (destroyed), then the
 // reconstruction into post-collision deviations v (PAIRS as collide_modes).
-template <typename R, bool PREDRAWN, bool PAIRS = true, typename A>
-__device__ __forceinline__ void noise_synthesise(R (&qm)[3][3][3], R rho, const A &a, const R (&nz)[kNoise],
-                                                 uint32_t node, R (&v)[3][3][3])
+template <typename V, bool PREDRAWN, bool PAIRS = true, typename A>
+__device__ __forceinline__ void noise_synthesise(V (&qm)[3][3][3], V rho, const A &a, const V (&nz)[kNoise],
+                                                 uint32_t node, V (&v)[3][3][3])
 {
     // a6: M_k += phi_k r_k for k = 4..26 with phi_k = sqrt(rho) amp
     // sqrt(b_k / c_s^2) (amp_h for k = 4..9, amp_g for the ghosts)
     {
-        const R sr = a.noise_rho0 ? a.sqrt_rho0 : sqrt_(rho);
-        const R sh = sr * a.amp_h, sg = sr * a.amp_g;
+        const V sr = a.noise_rho0 ? vbc(a.sqrt_rho0, rho) : sqrt_(rho);
+        const V sh = vmul(sr, vbc(a.amp_h, rho)), sg = vmul(sr, vbc(a.amp_g, rho));
         if (PREDRAWN) {
 #pragma unroll
             for (int mk = 4; mk < kQ; ++mk) {
                 const int d = mode_deg(mk);
-                qm[d % 3][(d / 3) % 3][d / 9] += (mk <= 9 ? sh : sg) * nz[mk - 4];
+                V &q = qm[d % 3][(d / 3) % 3][d / 9];
+                q = vfma(mk <= 9 ? sh : sg, nz[mk - 4], q);
             }
         } else {
             // pairs never mix hydrodynamic and ghost modes
 #pragma unroll
             for (int blk = 0; blk < 6; ++blk) {
-                const u32x4 o = noise_block(a, node, blk);
-                R rad0, c0, s0, rad1, c1, s1;
-                box_muller(o.x, o.y, rad0, c0, s0);
-                box_muller(o.z, o.w, rad1, c1, s1);
-                const R trig[4] = {c0, s0, c1, s1};
+                V rad0, c0, s0, rad1, c1, s1;
+                block_normals(a, node, blk, rad0, c0, s0, rad1, c1, s1);
+                const V trig[4] = {c0, s0, c1, s1};
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     const int mk = 4 + 4 * blk + m;
                     if (mk < kQ) {
                         const int d = mode_deg(mk);
-                        const int di = d % 3, dj = (d / 3) % 3, dk = d / 9;
-                        const R kk = R(syn_scale(di, dj, dk) * sqrt_b_over_cs2(di, dj, dk));
                         // same rounding order as draw_noise + the PREDRAWN branch
-                        const R t = ((m < 2 ? rad0 : rad1) * kk) * trig[m];
-                        qm[di][dj][dk] += (mk <= 9 ? sh : sg) * t;
+                        const V t = vmul(vmul(m < 2 ? rad0 : rad1, vset<V>(noise_scale(mk))), trig[m]);
+                        V &q = qm[d % 3][(d / 3) % 3][d / 9];
+                        q = vfma(mk <= 9 ? sh : sg, t, q);
                     }
                 }
             }
@@ -514,19 +611,20 @@ __device__ __forceinline__ void noise_synthesise(R (&qm)[3][3][3], R rho, const 
             for (int k = 0; k < 3; ++k) v[i][j][k] = qm[i][j][k];
 }
 
-// a2-a7, a9: collision of one node.  v[cx+1][cy+1][cz+1] holds the incoming
-// deviations on entry and the post-collision deviations on exit.
-// PREDRAWN: nz holds the node's scaled normals (draw_noise, drawn before the
-// populations arrived); otherwise the normals of `node` are drawn here pair
-// by pair and folded in at once (fewer live registers).
-template <typename R, int SCHEME, bool STATS, bool PREDRAWN, typename A>
-__device__ __forceinline__ void collide_core(R (&v)[3][3][3], const A &a,
-                                             const R (&nz)[kNoise], uint32_t node, R (&acc)[NSTAT])
+// a2-a7, a9: collision of one node (V = float2: of nodes node and node + 1,
+// one per lane).  v[cx+1][cy+1][cz+1] holds the incoming deviations on entry
+// and the post-collision deviations on exit.  PREDRAWN: nz holds the node's
+// scaled normals (draw_noise, drawn before the populations arrived);
+// otherwise the normals of `node` are drawn here pair by pair and folded in
+// at once (fewer live registers).
+template <typename V, int SCHEME, bool STATS, bool PREDRAWN, typename A>
+__device__ __forceinline__ void collide_core(V (&v)[3][3][3], const A &a,
+                                             const V (&nz)[kNoise], uint32_t node, V (&acc)[NSTAT])
 {
-    R qm[3][3][3];
-    R rho, dj[4];
-    collide_modes<R, SCHEME, STATS>(v, a, acc, qm, rho, dj);
-    noise_synthesise<R, PREDRAWN>(qm, rho, a, nz, node, v);
+    V qm[3][3][3];
+    V rho, dj[4];
+    collide_modes<V, SCHEME, STATS, !std::is_same<V, float2>::value>(v, a, acc, qm, rho, dj);
+    noise_synthesise<V, PREDRAWN, !std::is_same<V, float2>::value>(qm, rho, a, nz, node, v);
 }
 
 // ---------------------------------------------------------------------------
@@ -633,22 +731,26 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  "r"(bytes)
                  : "memory");
 }
-// Bounded wait for the phase with the given parity: each poll suspends for
-// at most 1 us (suspend-time hint), and the wait gives up after 2^20 polls
-// (about one second) and returns false.
+// Bounded wait for the phase with the given parity: a poll that finds the
+// phase open sleeps before the next one, 64 ns doubling to 512 ns (a warp
+// that waits burns few issue slots of its sub-partition), and the wait gives
+// up after 2^21 polls (at least half a second) and returns false.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {
     const uint32_t addr = smem_u32(bar);
-    for (uint32_t it = 0; it < (1u << 20); ++it) {
+    uint32_t ns = 64;
+    for (uint32_t it = 0; it < (1u << 21); ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n"
-            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
             " selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(addr), "r"(parity), "r"(1000u)
+            : "r"(addr), "r"(parity)
             : "memory");
         if (done) return true;
+        __nanosleep(ns);
+        ns = ns < 512 ? 2 * ns : 512;
     }
     return false;
 }
@@ -684,7 +786,31 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 #define FLBM_ROW_COMPUTE 256
 #endif
 constexpr int kRowCompute = FLBM_ROW_COMPUTE;
-constexpr int kRowStages = 2;      // shared-memory stages (rows in flight)
+constexpr int kRowStages = 2;      // shared-memory stages (rows in flight), one node per thread
+// Two nodes per thread (FP32 and FP16 storage): CTAs of 4 compute warps,
+// several per SM (so that one CTA's row waits overlap the others' work),
+// each with 4 shared-memory stages where they fit its share of the SM, else 2.
+constexpr int kRowPairCompute = 128;
+constexpr int kRowMaxStages = 4;
+// CTAs per SM of the two-node kernel: 3 for FP16 storage (128 registers), 2
+// for FP32 (whose 512-wide rows leave shared memory for two); the stages of
+// one CTA share an equal part of two stages of a 512-wide FP32 row per CTA
+// of a pair of CTAs.
+template <typename S> constexpr int row_pair_ctas() { return sizeof(S) == 2 ? 3 : 2; }
+constexpr size_t kRowPairSmSmem = size_t(4) * 27 * 512 * 4;
+
+// Adjacent pair (x, x+1) of a staged segment (x even): one 64-bit or 32-bit
+// shared access.
+__device__ __forceinline__ float2 ld_pair(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ float2 ld_pair(const __half *p)
+{
+    return __half22float2(*reinterpret_cast<const __half2 *>(p));
+}
+__device__ __forceinline__ void st_pair(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+__device__ __forceinline__ void st_pair(__half *p, float2 v)
+{
+    *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v);
+}
 
 // Shared staging of a row CTA per stage: 27 segments of nx elements.
 template <typename S>
@@ -718,15 +844,23 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 
 // Warp-specialised row pipeline.  Warps 0..nc/32-1 collide; the last warp
 // is the producer: its lanes 0..26 each move one of the 27 segments of a row
-// (bulk load into stage k % kRowStages, completing on full[s]; after the
-// compute warps release the stage through empty[s], bulk store back to HBM).
-// Every wait is bounded; a wait that runs out sets flag bit 1 and stops.
-template <typename S, typename R, int SCHEME, bool ODD, bool STATS>
-__global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) <= 4 ? 2 : 1)
-    k_step_rows(S *__restrict__ g, const StepArgs<R> a)
+// (bulk load into stage k % nst, completing on full[s]; after the compute
+// warps release the stage through empty[s], bulk store back to HBM).  Every
+// wait is bounded; a wait that runs out sets flag bit 1 and stops.
+// NP = 1: a compute thread collides one node at a time, its normals drawn
+// while the row lands; NP = 2 (FP32 arithmetic): it collides the adjacent
+// nodes (x, x+1) at once as packed FP32 pairs, and moves each unshifted
+// segment value pair with one shared access.
+template <typename S, typename R, int SCHEME, bool ODD, bool STATS, int NP>
+__global__ void __launch_bounds__(NP == 2 ? kRowPairCompute + 32 : kRowCompute + 32,
+                                  NP == 2 ? row_pair_ctas<S>() : (sizeof(S) <= 4 ? 2 : 1))
+    k_step_rows(S *__restrict__ g, const StepArgs<R> a, uint32_t nst_log2)
 {
+    using V = typename std::conditional<NP == 2, float2, R>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[kRowStages], empty[kRowStages];
+    __shared__ __align__(8) uint64_t full[kRowMaxStages], empty[kRowMaxStages];
+    // stages: a power of two, nst = 1 << nst_log2 <= kRowMaxStages
+    const uint32_t nst = 1u << nst_log2, st_mask = nst - 1;
     __shared__ TotSlot<R> tot[32][NSTAT];
     S *const stage = reinterpret_cast<S *>(smem_raw);
     const uint32_t nx = a.nx;
@@ -735,12 +869,12 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) <= 4 ? 2 : 1)
     const uint32_t seg_bytes = nx * uint32_t(sizeof(S));
     const uint64_t nrows = uint64_t(a.ny) * a.nz;
     const uint32_t lane = threadIdx.x & 31;
-    R acc[NSTAT];
+    V acc[NSTAT];
 #pragma unroll
-    for (int s = 0; s < NSTAT; ++s) acc[s] = R(0);
+    for (int s = 0; s < NSTAT; ++s) acc[s] = vset<V>(0.0);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kRowStages; ++s) {
+        for (uint32_t s = 0; s < nst; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], nc / 32);
         }
@@ -756,8 +890,8 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) <= 4 ? 2 : 1)
         bool ok = true;
         // store of row number kk (this CTA's kk-th row) out of its stage
         auto store_row = [&](uint64_t kk) {
-            const int s = int(kk % kRowStages);
-            ok = mbar_wait(&empty[s], uint32_t((kk / kRowStages) & 1));
+            const int s = int(kk & st_mask);
+            ok = mbar_wait(&empty[s], uint32_t((kk >> nst_log2) & 1));
             if (!ok) return;
             const uint64_t row = blockIdx.x + kk * gridDim.x;
             if (d < kQ) {
@@ -771,9 +905,9 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) <= 4 ? 2 : 1)
         for (;; ++k) {
             const uint64_t row = blockIdx.x + k * gridDim.x;
             if (row >= nrows) break;
-            const int s = int(k % kRowStages);
-            if (k >= kRowStages) {
-                store_row(k - kRowStages);
+            const int s = int(k & st_mask);
+            if (k >= nst) {
+                store_row(k - nst);
                 if (!ok) break;
             }
             if (lane == 0) {
@@ -786,22 +920,75 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) <= 4 ? 2 : 1)
                          seg_bytes, &full[s]);
         }
         // drain the last stages
-        for (uint64_t kk = (k > kRowStages ? k - kRowStages : 0); ok && kk < k; ++kk) store_row(kk);
+        for (uint64_t kk = (k > nst ? k - nst : 0); ok && kk < k; ++kk) store_row(kk);
         if (!ok && lane == 0) atomicOr(a.flag, 2u);
         if (d < kQ) bulk_wait_all();
-    } else {
-        // ---------------- compute warps ----------------
+    } else if constexpr (NP == 2) {
+        // ---------------- compute warps, two nodes per thread ----------------
         for (uint64_t k = 0;; ++k) {
             const uint64_t row = blockIdx.x + k * gridDim.x;
             if (row >= nrows) break;
-            const int s = int(k % kRowStages);
+            const int s = int(k & st_mask);
+            const uint32_t y = uint32_t(row % a.ny), z = uint32_t(row / a.ny);
+            const uint32_t rowbase = nx * (y + a.ny * z);
+            // the outcome is made warp-uniform: warp_flush needs every lane
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[s], uint32_t((k >> nst_log2) & 1)))) {
+                if (lane == 0) atomicOr(a.flag, 2u);
+                break;
+            }
+            S *st = stage + size_t(s) * stage_elems;
+            for (uint32_t x = 2 * threadIdx.x; x < nx; x += 2 * nc) {
+                // periodic x-1, x, x+1 of the nodes x (lane .x) and x+1 (lane .y);
+                // x is even and nx a multiple of 32, so x+1 < nx
+                const uint32_t xa[3] = {x ? x - 1 : nx - 1, x, x + 1};
+                const uint32_t xb[3] = {x, x + 1, (x + 2 < nx) ? x + 2 : 0};
+                // a1: incoming f_c from segment d(c) at x (even) / x - c_x (odd)
+                V v[3][3][3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+#pragma unroll
+                        for (int kk = 0; kk < 3; ++kk) {
+                            const S *seg = st + (9 * i + 3 * j + kk) * nx;
+                            if (!ODD || i == 1) v[i][j][kk] = ld_pair(seg + x);
+                            else v[i][j][kk] = make_float2(stage_ld(seg[xa[2 - i]]), stage_ld(seg[xb[2 - i]]));
+                        }
+                V nz[kNoise];   // unused: the normals are drawn inside, pair by pair
+                collide_core<V, SCHEME, STATS, false>(v, a, nz, rowbase + x, acc);
+                // a8: f*_c to segment d(-c) at x (even) / x + c_x (odd)
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+#pragma unroll
+                        for (int kk = 0; kk < 3; ++kk) {
+                            S *seg = st + (9 * (2 - i) + 3 * (2 - j) + (2 - kk)) * nx;
+                            if (!ODD || i == 1) st_pair(seg + x, v[i][j][kk]);
+                            else {
+                                seg[xa[i]] = stage_st<S>(v[i][j][kk].x);
+                                seg[xb[i]] = stage_st<S>(v[i][j][kk].y);
+                            }
+                        }
+            }
+            fence_proxy_async_smem();   // generic-proxy writes before the bulk store reads
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            if (STATS && k % kFlushEvery == kFlushEvery - 1) warp_flush(acc, tot);
+        }
+    } else {
+        // ---------------- compute warps, one node per thread ----------------
+        for (uint64_t k = 0;; ++k) {
+            const uint64_t row = blockIdx.x + k * gridDim.x;
+            if (row >= nrows) break;
+            const int s = int(k & st_mask);
             const uint32_t y = uint32_t(row % a.ny), z = uint32_t(row / a.ny);
             const uint32_t rowbase = nx * (y + a.ny * z);
             // the first node's normals are drawn while the row's segments land
             R nz[kNoise];
             if (threadIdx.x < nx) draw_noise(a, rowbase + threadIdx.x, nz);
             // the outcome is made warp-uniform: warp_flush needs every lane
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[s], uint32_t((k / kRowStages) & 1)))) {
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[s], uint32_t((k >> nst_log2) & 1)))) {
                 if (lane == 0) atomicOr(a.flag, 2u);
                 break;
             }
@@ -850,25 +1037,63 @@ __global__ void __launch_bounds__(kRowCompute + 32, sizeof(S) <= 4 ? 2 : 1)
 // Dynamic shared memory of a row-pipeline CTA at most.
 constexpr size_t kRowMaxSmem = 200 * 1024;
 
-// Whether the row pipeline serves a box of row length nx, and its CTA shape.
+// Whether the two-node row kernel may serve FP32 / FP16 storage:
+// FLBM_ROW_PAIRS=0 (environment, read at every launch) keeps one node per
+// thread (a measuring knob; the default is two).  Both give the same bits.
+inline bool row_pairs_enabled()
+{
+    const char *e = std::getenv("FLBM_ROW_PAIRS");
+    return !(e && std::atoi(e) == 0);
+}
+
+// Whether the row pipeline serves a box of row length nx, and its CTA shape:
+// np nodes per compute thread, 1 << stages_log2 shared-memory stages.
 struct RowPlan {
     bool use = false;
     int threads = 0;
     size_t smem = 0;
+    int np = 1;
+    uint32_t stages_log2 = 1;
 };
 template <typename S>
 inline RowPlan row_plan(uint32_t nx)
 {
     RowPlan p;
-    const size_t smem = kRowStages * row_stage_bytes<S>(nx);
-    if (nx % 32 != 0 || nx < 32 || smem > kRowMaxSmem) return p;
-    const uint32_t npt = (nx + kRowCompute - 1) / kRowCompute;
-    uint32_t thr = (nx + npt - 1) / npt;
+    if (nx % 32 != 0 || nx < 32) return p;
+    const size_t sb = row_stage_bytes<S>(nx);
+    uint32_t cmax = kRowCompute;
+    // pairs from rows of 256 nodes (a full CTA of 4 compute warps); narrower
+    // rows run faster with one node per thread (measured at 128^3)
+    const size_t cta_smem = kRowPairSmSmem / size_t(row_pair_ctas<S>());
+    if (!std::is_same<S, double>::value && row_pairs_enabled() && nx >= 2 * kRowPairCompute &&
+        2 * sb <= cta_smem) {
+        p.np = 2;
+        p.stages_log2 = (size_t(kRowMaxStages) * sb <= cta_smem) ? 2 : 1;
+        cmax = kRowPairCompute;
+    }
+    const size_t smem = (size_t(1) << p.stages_log2) * sb;
+    if (smem > kRowMaxSmem) return p;
+    const uint32_t units = nx / uint32_t(p.np);       // nodes or node pairs of a row
+    const uint32_t npt = (units + cmax - 1) / cmax;
+    uint32_t thr = (units + npt - 1) / npt;
     thr = (thr + 31) / 32 * 32;
     p.use = true;
     p.threads = int(thr) + 32;   // compute warps + the producer warp
     p.smem = smem;
     return p;
+}
+
+// One launch of the row kernel variant that plan rp picks.
+template <typename S, typename R, int SC, bool OD, bool ST>
+void launch_rows(S *g, const StepArgs<R> &a, const RowPlan &rp, int row_grid, cudaStream_t s)
+{
+    if constexpr (!std::is_same<S, double>::value) {
+        if (rp.np == 2) {
+            k_step_rows<S, R, SC, OD, ST, 2><<<row_grid, rp.threads, rp.smem, s>>>(g, a, rp.stages_log2);
+            return;
+        }
+    }
+    k_step_rows<S, R, SC, OD, ST, 1><<<row_grid, rp.threads, rp.smem, s>>>(g, a, rp.stages_log2);
 }
 
 template <typename S, typename R, typename I>
@@ -877,8 +1102,7 @@ cudaError_t launch_step_t(S *g, const StepArgs<R> &a, int scheme, bool odd, bool
 {
     const RowPlan rp = row_plan<S>(a.nx);
     if (rp.use && row_grid > 0) {
-#define FLBM_LAUNCH_ROWS(SC, OD, ST) \
-    k_step_rows<S, R, SC, OD, ST><<<row_grid, rp.threads, rp.smem, s>>>(g, a)
+#define FLBM_LAUNCH_ROWS(SC, OD, ST) launch_rows<S, R, SC, OD, ST>(g, a, rp, row_grid, s)
         if (scheme == 0) {
             if (odd) { if (stats) FLBM_LAUNCH_ROWS(0, true, true); else FLBM_LAUNCH_ROWS(0, true, false); }
             else     { if (stats) FLBM_LAUNCH_ROWS(0, false, true); else FLBM_LAUNCH_ROWS(0, false, false); }
@@ -907,6 +1131,24 @@ cudaError_t launch_step_t(S *g, const StepArgs<R> &a, int scheme, bool odd, bool
     return cudaGetLastError();
 }
 
+// Opts the four row kernels of one variant into kRowMaxSmem bytes of dynamic
+// shared memory and returns the resident CTAs per SM of the larger
+// (reducing, odd-form) one for plan rp.
+template <typename S, typename R, int SC, int NP>
+int prepare_rows(const RowPlan &rp, bool stats)
+{
+    const int dmax = int(kRowMaxSmem);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, false, false, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, false, true, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, true, false, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, true, true, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
+    int nb = 0;
+    const cudaError_t e =
+        stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<S, R, SC, true, true, NP>, rp.threads, rp.smem)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<S, R, SC, true, false, NP>, rp.threads, rp.smem);
+    return (e == cudaSuccess && nb > 0) ? nb : 0;
+}
+
 // Resident CTAs per SM of the larger (reducing, odd-form) variant of each
 // kernel; also opts the row kernels into their shared memory on the current
 // device.  rows = 0 when the row pipeline does not serve the box.
@@ -924,15 +1166,13 @@ void prepare_scheme(uint32_t nx, bool stats, int &direct, int &rows)
     if (!rp.use) return;
     // the attribute is per kernel, shared by every context of the process:
     // set it to the largest staging any box may use, not to this box's
-    const int sm = int(kRowMaxSmem);
-    cudaFuncSetAttribute(k_step_rows<S, R, SC, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_step_rows<S, R, SC, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_step_rows<S, R, SC, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_step_rows<S, R, SC, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    nb = 0;
-    e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<S, R, SC, true, true>, rp.threads, rp.smem)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<S, R, SC, true, false>, rp.threads, rp.smem);
-    if (e == cudaSuccess && nb > 0) rows = nb;
+    if constexpr (!std::is_same<S, double>::value) {
+        if (rp.np == 2) {
+            rows = prepare_rows<S, R, SC, 2>(rp, stats);
+            return;
+        }
+    }
+    rows = prepare_rows<S, R, SC, 1>(rp, stats);
 }
 
 template <typename S, typename R, typename I>

@@ -19,12 +19,14 @@ FP16 deviations g_i = f_i - w_i rho0 are read exactly):
 * u_a = j_a (1/rho) with rho = rho0 + drho (one rounding) and the hardware
   reciprocal (within 2 ulp): |du| <= (E + |u| (E + u rho)) / rho + 6 u |u|,
   and u_a^2 as a square;
-* accumulation: every thread adds its nodes' terms in FP32, at most m of
-  them before its warp adds the 32 threads' sums in five FP32 levels into an
-  FP64 total (every 8 rows of the row pipeline, every 8 chunks of the direct
-  kernel); blocks and the grid add in FP64:
-  gamma(m + 6) sum_n (|x_n| + e_n), gamma(k) = k u / (1 - k u).
-The bound is sum_n e_n + gamma(m + 6) sum_n (|x_n| + e_n).
+* accumulation: every thread adds its nodes' terms in FP32 (a two-node
+  thread in two lanes, added once at the end), at most m of them before its
+  warp adds the 32 threads' sums in five FP32 levels into its slot (every 8
+  rows of the row pipeline, every 8 chunks of the direct kernel), a slot
+  kept exactly as an unevaluated pair of FP32 numbers (TwoSum); blocks and
+  the grid add in FP64: gamma(m + 7) sum_n (|x_n| + e_n),
+  gamma(k) = k u / (1 - k u).
+The bound is sum_n e_n + gamma(m + 7) sum_n (|x_n| + e_n).
 """
 import numpy as np
 
@@ -70,7 +72,7 @@ def sums_and_bounds(oracle_mod, f, rho0, m_per_thread):
     """FP64 sums S[13] of the per-node terms and the bound B[13] on the FP32
     path's |S_gpu - S| when no thread adds more than m_per_thread nodes."""
     x, e = node_terms(oracle_mod, f, rho0)
-    g = _gamma(m_per_thread + 6)
+    g = _gamma(m_per_thread + 7)
     return x.sum(1), e.sum(1) + g * (np.abs(x) + e).sum(1)
 
 
@@ -78,12 +80,13 @@ FLUSH_EVERY = 8
 
 
 def nodes_per_thread_bound(nx, ny, nz):
-    """Nodes any thread of the step kernels adds in FP32 at most before its
-    warp folds the sums into FP64, for a GB300's 152 SMs: the row pipeline
+    """Nodes any thread (or lane) of the step kernels adds in FP32 at most
+    before its warp folds the sums, for a GB300's 152 SMs: the row pipeline
     gives each CTA ceil(rows / grid) rows, each thread ceil(nx / 256) nodes
-    of a row, and flushes every 8 rows; the direct kernel one node per
-    128-node chunk, ceil(chunks / grid) chunks, flushed every 8 chunks; both
-    grids hold at least min(work, 152) CTAs."""
+    of a row (one-node kernel) or ceil(nx / 256) pairs, one node of each per
+    lane (two-node kernel), and flushes every 8 rows; the direct kernel one
+    node per 128-node chunk, ceil(chunks / grid) chunks, flushed every 8
+    chunks; every grid holds at least min(work, 152) CTAs."""
     rows = ny * nz
     chunks = -(-nx // 128) * rows
     row_kernel = min(-(-rows // min(rows, 152)), FLUSH_EVERY) * -(-nx // 256)
