@@ -418,6 +418,12 @@ void step_grids(const flbm_params &p, int nsm, int occ, int occ_rows, int &grid,
     }
 }
 
+bool row_pairs_enabled()
+{
+    const char *e = std::getenv("FLBM_ROW_PAIRS");
+    return !(e && std::atoi(e) == 0);
+}
+
 void fill_step_constants(const flbm_params &p, StepArgs<float> &a) { fill_constants_t<float>(p, a); }
 void fill_step_constants(const flbm_params &p, StepArgs<double> &a) { fill_constants_t<double>(p, a); }
 void set_thread_error(const char *msg) { g_create_error = msg; }

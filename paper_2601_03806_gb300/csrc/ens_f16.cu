@@ -5,14 +5,16 @@
 namespace flbm {
 
 cudaError_t launch_ens_step_f16(const EnsArgs &a, int scheme, bool odd, bool stats, int grid, int threads,
-                                size_t smem, cudaStream_t s)
+                                size_t smem, cudaStream_t s, int np)
 {
-    return launch_ens_step_t<__half, float>(a, scheme, odd, stats, grid, threads, smem, s);
+    if (np == 2) return launch_ens_step_f16p(a, scheme, odd, stats, grid, threads, smem, s);
+    return launch_ens_step_t<__half, float, 1>(a, scheme, odd, stats, grid, threads, smem, s);
 }
 
-int ens_occupancy_f16(int scheme, int threads, size_t smem)
+int ens_occupancy_f16(int scheme, int threads, size_t smem, int np)
 {
-    return ens_occupancy_t<__half, float>(scheme, threads, smem);
+    if (np == 2) return ens_occupancy_f16p(scheme, threads, smem);
+    return ens_occupancy_t<__half, float, 1>(scheme, threads, smem);
 }
 
 }  // namespace flbm

@@ -5,14 +5,16 @@
 namespace flbm {
 
 cudaError_t launch_ens_step_f32(const EnsArgs &a, int scheme, bool odd, bool stats, int grid, int threads,
-                                size_t smem, cudaStream_t s)
+                                size_t smem, cudaStream_t s, int np)
 {
-    return launch_ens_step_t<float, float>(a, scheme, odd, stats, grid, threads, smem, s);
+    if (np == 2) return launch_ens_step_f32p(a, scheme, odd, stats, grid, threads, smem, s);
+    return launch_ens_step_t<float, float, 1>(a, scheme, odd, stats, grid, threads, smem, s);
 }
 
-int ens_occupancy_f32(int scheme, int threads, size_t smem)
+int ens_occupancy_f32(int scheme, int threads, size_t smem, int np)
 {
-    return ens_occupancy_t<float, float>(scheme, threads, smem);
+    if (np == 2) return ens_occupancy_f32p(scheme, threads, smem);
+    return ens_occupancy_t<float, float, 1>(scheme, threads, smem);
 }
 
 cudaError_t launch_ens_post(const EnsArgs &a, bool stats, uint32_t cwarps, unsigned int *done,

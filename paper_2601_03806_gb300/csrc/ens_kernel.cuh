@@ -140,14 +140,17 @@ __device__ __forceinline__ void ens_item(const EnsReplica &rp, uint64_t i, uint3
     y0 = (j - z * rp.items_per_plane) * rp.rpi;
 }
 
-// At most 112 registers a thread (the collision spills little at that cap).
-// Registers are split over the SM's four sub-partitions, so two CTAs fit an
-// SM up to 7 compute warps each; two CTAs of 8 + 1 warps would need <= 96.
+// NP = 1: one node per compute thread, at most 112 registers a thread (the
+// collision spills little at that cap; registers are split over the SM's four
+// sub-partitions, so two CTAs fit an SM up to 7 compute warps each).  NP = 2:
+// two adjacent nodes of a row per thread as packed FP32 pairs (row lengths
+// are even: a replica's rows are 16-byte aligned), at most 168 registers, so
+// two CTAs of up to 4 compute warps fit an SM.
 // STRIDE: the stage stride as a compile-time constant (256 or 512 nodes, the
 // common tunings), which folds the 27 segment offsets of a node's shared
 // loads and stores into their immediates; 0 reads it from the arguments.
-template <typename S, typename R, int SCHEME, bool ODD, bool STATS, int STRIDE = 0>
-__global__ void __maxnreg__(112) k_step_ens(const __grid_constant__ EnsArgs a)
+template <typename S, typename R, int SCHEME, bool ODD, bool STATS, int STRIDE = 0, int NP = 1>
+__global__ void __maxnreg__(NP == 2 ? 168 : 112) k_step_ens(const __grid_constant__ EnsArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kEnsMaxStages], empty[kEnsMaxStages];
@@ -231,11 +234,12 @@ __global__ void __maxnreg__(112) k_step_ens(const __grid_constant__ EnsArgs a)
         if (d < kQ) bulk_wait_all();
     } else {
         // ---------------- compute warps ----------------
+        using V = typename std::conditional<NP == 2, float2, R>::type;
         const uint64_t step = *a.dstep;
         const uint32_t warp = threadIdx.x >> 5;
-        R acc[NSTAT];
+        V acc[NSTAT];
 #pragma unroll
-        for (int s = 0; s < NSTAT; ++s) acc[s] = R(0);
+        for (int s = 0; s < NSTAT; ++s) acc[s] = vset<V>(0.0);
         uint32_t r = r0;
         uint32_t s = 0, ph = 0;   // stage and mbarrier phase of item k
         for (uint32_t k = 0; k < nk; ++k) {
@@ -252,38 +256,78 @@ __global__ void __maxnreg__(112) k_step_ens(const __grid_constant__ EnsArgs a)
             // of its exact value and at least 1/(2 nx) >= 5.6e-4 from an
             // integer (l < 4096, nx <= 896), so truncation gives l / nx exactly
             const float inv_nx = __frcp_rn(float(nx));
-            R nz[kNoise];
-            if (threadIdx.x < item_nodes) draw_noise(v, base + threadIdx.x, nz);
-            if (!mbar_wait(&full[s], ph)) {
-                if (lane == 0) atomicOr(a.flag, 2u);
-                break;
-            }
-            S *st = stage + size_t(s) * stage_elems;
-            for (uint32_t l = threadIdx.x; l < item_nodes; l += nc) {
-                if (l != threadIdx.x) draw_noise(v, base + l, nz);
-                const uint32_t t = uint32_t((float(l) + 0.5f) * inv_nx), x = l - t * nx, rb = t * nx;
-                const uint32_t xsh[3] = {rb + (x ? x - 1 : nx - 1), l, rb + ((x + 1 < nx) ? x + 1 : 0)};
-                R vv[3][3][3];
+            if constexpr (NP == 2) {
+                if (!mbar_wait(&full[s], ph)) {
+                    if (lane == 0) atomicOr(a.flag, 2u);
+                    break;
+                }
+                S *st = stage + size_t(s) * stage_elems;
+                for (uint32_t l = 2 * threadIdx.x; l < item_nodes; l += 2 * nc) {
+                    // nodes l (lane .x) and l + 1 (lane .y) of one row: l and nx are even
+                    const uint32_t t = uint32_t((float(l) + 0.5f) * inv_nx), x = l - t * nx, rb = t * nx;
+                    const uint32_t xa[3] = {rb + (x ? x - 1 : nx - 1), l, l + 1};
+                    const uint32_t xb[3] = {l, l + 1, rb + ((x + 2 < nx) ? x + 2 : 0)};
+                    V vv[3][3][3];
 #pragma unroll
-                for (int ci = 0; ci < 3; ++ci)
+                    for (int ci = 0; ci < 3; ++ci)
 #pragma unroll
-                    for (int cj = 0; cj < 3; ++cj)
+                        for (int cj = 0; cj < 3; ++cj)
 #pragma unroll
-                        for (int ck = 0; ck < 3; ++ck) {
-                            const uint32_t pos = ODD ? xsh[2 - ci] : l;
-                            vv[ci][cj][ck] = R(stage_ld(st[(9 * ci + 3 * cj + ck) * stride + pos]));
-                        }
-                collide_core<R, SCHEME, STATS, true>(vv, v, nz, base + l, acc);
+                            for (int ck = 0; ck < 3; ++ck) {
+                                const S *seg = st + (9 * ci + 3 * cj + ck) * stride;
+                                if (!ODD || ci == 1) vv[ci][cj][ck] = ld_pair(seg + l);
+                                else vv[ci][cj][ck] = make_float2(stage_ld(seg[xa[2 - ci]]), stage_ld(seg[xb[2 - ci]]));
+                            }
+                    V nzp[kNoise];   // unused: the normals are drawn inside, pair by pair
+                    collide_core<V, SCHEME, STATS, false>(vv, v, nzp, base + l, acc);
 #pragma unroll
-                for (int ci = 0; ci < 3; ++ci)
+                    for (int ci = 0; ci < 3; ++ci)
 #pragma unroll
-                    for (int cj = 0; cj < 3; ++cj)
+                        for (int cj = 0; cj < 3; ++cj)
 #pragma unroll
-                        for (int ck = 0; ck < 3; ++ck) {
-                            const uint32_t pos = ODD ? xsh[ci] : l;
-                            st[(9 * (2 - ci) + 3 * (2 - cj) + (2 - ck)) * stride + pos] =
-                                stage_st<S>(vv[ci][cj][ck]);
-                        }
+                            for (int ck = 0; ck < 3; ++ck) {
+                                S *seg = st + (9 * (2 - ci) + 3 * (2 - cj) + (2 - ck)) * stride;
+                                if (!ODD || ci == 1) st_pair(seg + l, vv[ci][cj][ck]);
+                                else {
+                                    seg[xa[ci]] = stage_st<S>(vv[ci][cj][ck].x);
+                                    seg[xb[ci]] = stage_st<S>(vv[ci][cj][ck].y);
+                                }
+                            }
+                }
+            } else {
+                R nz[kNoise];
+                if (threadIdx.x < item_nodes) draw_noise(v, base + threadIdx.x, nz);
+                if (!mbar_wait(&full[s], ph)) {
+                    if (lane == 0) atomicOr(a.flag, 2u);
+                    break;
+                }
+                S *st = stage + size_t(s) * stage_elems;
+                for (uint32_t l = threadIdx.x; l < item_nodes; l += nc) {
+                    if (l != threadIdx.x) draw_noise(v, base + l, nz);
+                    const uint32_t t = uint32_t((float(l) + 0.5f) * inv_nx), x = l - t * nx, rb = t * nx;
+                    const uint32_t xsh[3] = {rb + (x ? x - 1 : nx - 1), l, rb + ((x + 1 < nx) ? x + 1 : 0)};
+                    R vv[3][3][3];
+#pragma unroll
+                    for (int ci = 0; ci < 3; ++ci)
+#pragma unroll
+                        for (int cj = 0; cj < 3; ++cj)
+#pragma unroll
+                            for (int ck = 0; ck < 3; ++ck) {
+                                const uint32_t pos = ODD ? xsh[2 - ci] : l;
+                                vv[ci][cj][ck] = R(stage_ld(st[(9 * ci + 3 * cj + ck) * stride + pos]));
+                            }
+                    collide_core<R, SCHEME, STATS, true>(vv, v, nz, base + l, acc);
+#pragma unroll
+                    for (int ci = 0; ci < 3; ++ci)
+#pragma unroll
+                        for (int cj = 0; cj < 3; ++cj)
+#pragma unroll
+                            for (int ck = 0; ck < 3; ++ck) {
+                                const uint32_t pos = ODD ? xsh[ci] : l;
+                                st[(9 * (2 - ci) + 3 * (2 - cj) + (2 - ck)) * stride + pos] =
+                                    stage_st<S>(vv[ci][cj][ck]);
+                            }
+                }
             }
             fence_proxy_async_smem();   // generic-proxy writes before the bulk store reads
             __syncwarp();
@@ -298,9 +342,9 @@ __global__ void __maxnreg__(112) k_step_ens(const __grid_constant__ EnsArgs a)
                     double *out = a.partials + ((size_t(blockIdx.x) + r) * kEnsMaxWarps + warp) * NSTAT;
 #pragma unroll
                     for (int q = 0; q < NSTAT; ++q) {
-                        const R tot = warp_sum(acc[q]);
+                        const R tot = warp_sum(lane_total(acc[q]));
                         if (lane == 0) out[q] = double(tot);
-                        acc[q] = R(0);
+                        acc[q] = vset<V>(0.0);
                     }
                 }
             }
@@ -344,12 +388,12 @@ __global__ void k_ens_post(const __grid_constant__ EnsArgs a, uint32_t cwarps, u
 // ---------------------------------------------------------------------------
 // launchers
 
-template <typename S, typename R>
+template <typename S, typename R, int NP>
 cudaError_t launch_ens_step_t(const EnsArgs &a, int scheme, bool odd, bool stats, int grid, int threads,
                               size_t smem, cudaStream_t s)
 {
-#define FLBM_LAUNCH_ENS(SC, OD, ST) k_step_ens<S, R, SC, OD, ST><<<grid, threads, smem, s>>>(a)
-#define FLBM_LAUNCH_ENS_W(W, OD, ST) k_step_ens<S, R, 1, OD, ST, W><<<grid, threads, smem, s>>>(a)
+#define FLBM_LAUNCH_ENS(SC, OD, ST) k_step_ens<S, R, SC, OD, ST, 0, NP><<<grid, threads, smem, s>>>(a)
+#define FLBM_LAUNCH_ENS_W(W, OD, ST) k_step_ens<S, R, 1, OD, ST, W, NP><<<grid, threads, smem, s>>>(a)
     if (scheme == 1 && (a.stride == 512 || a.stride == 256)) {   // GMF at a compile-time stride
         if (a.stride == 512) {
             if (odd) { if (stats) FLBM_LAUNCH_ENS_W(512, true, true); else FLBM_LAUNCH_ENS_W(512, true, false); }
@@ -373,39 +417,39 @@ cudaError_t launch_ens_step_t(const EnsArgs &a, int scheme, bool odd, bool stats
     return cudaGetLastError();
 }
 
-template <typename S, typename R, int SC>
+template <typename S, typename R, int SC, int NP>
 int ens_occupancy_scheme(int threads, size_t smem)
 {
     // the attribute is per kernel and process-wide: the largest staging any
     // ensemble may use (occupancy below is for this shape's smem)
     const int sm = int(kRowMaxSmem);
-    cudaFuncSetAttribute(k_step_ens<S, R, SC, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_step_ens<S, R, SC, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_step_ens<S, R, SC, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_step_ens<S, R, SC, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_step_ens<S, R, SC, false, false, 0, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_step_ens<S, R, SC, false, true, 0, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_step_ens<S, R, SC, true, false, 0, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_step_ens<S, R, SC, true, true, 0, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (SC == 1) {
-        cudaFuncSetAttribute(k_step_ens<S, R, 1, false, false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaFuncSetAttribute(k_step_ens<S, R, 1, false, true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaFuncSetAttribute(k_step_ens<S, R, 1, true, false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaFuncSetAttribute(k_step_ens<S, R, 1, true, true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaFuncSetAttribute(k_step_ens<S, R, 1, false, false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaFuncSetAttribute(k_step_ens<S, R, 1, false, true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaFuncSetAttribute(k_step_ens<S, R, 1, true, false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaFuncSetAttribute(k_step_ens<S, R, 1, true, true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, false, false, 256, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, false, true, 256, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, true, false, 256, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, true, true, 256, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, false, false, 512, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, false, true, 512, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, true, false, 512, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_step_ens<S, R, 1, true, true, 512, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_ens<S, R, SC, true, true>, threads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_ens<S, R, SC, true, true, 0, NP>, threads, smem) !=
         cudaSuccess)
         return 0;
     return nb;
 }
 
-template <typename S, typename R>
+template <typename S, typename R, int NP>
 int ens_occupancy_t(int scheme, int threads, size_t smem)
 {
-    if (scheme == 0) return ens_occupancy_scheme<S, R, 0>(threads, smem);
-    if (scheme == 1) return ens_occupancy_scheme<S, R, 1>(threads, smem);
-    return ens_occupancy_scheme<S, R, 2>(threads, smem);
+    if (scheme == 0) return ens_occupancy_scheme<S, R, 0, NP>(threads, smem);
+    if (scheme == 1) return ens_occupancy_scheme<S, R, 1, NP>(threads, smem);
+    return ens_occupancy_scheme<S, R, 2, NP>(threads, smem);
 }
 
 }  // namespace flbm

@@ -48,6 +48,7 @@ struct flbm_ensemble {
     int grid = 0;
     int threads = 0;
     size_t smem = 0;
+    int np = 1;                        // nodes per compute thread of the step kernel
     int64_t step = 0;
     bool use_graph = true;
     cudaGraphExec_t gexec = nullptr;
@@ -80,8 +81,8 @@ size_t elem_bytes(int prec) { return prec == FLBM_FP16 ? 2 : 4; }
 
 int occupancy(const flbm_ensemble *e, int threads, size_t smem)
 {
-    return e->p0.precision == FLBM_FP32 ? ens_occupancy_f32(e->p0.scheme, threads, smem)
-                                        : ens_occupancy_f16(e->p0.scheme, threads, smem);
+    return e->p0.precision == FLBM_FP32 ? ens_occupancy_f32(e->p0.scheme, threads, smem, e->np)
+                                        : ens_occupancy_f16(e->p0.scheme, threads, smem, e->np);
 }
 
 std::string validate_ensemble(const flbm_params *params, int count)
@@ -140,6 +141,9 @@ int apply_tuning(flbm_ensemble *e, const flbm_ensemble_tuning &t)
     const size_t smem = size_t(t.stages) * kQ * stride * elem_bytes(e->p0.precision);
     if (smem > kMaxStageBytes) return efail(e, FLBM_E_INVALID, "tuning needs too much shared memory");
     const int threads = t.compute_warps * 32 + 32;
+    // two adjacent nodes per compute thread (packed FP32 pairs) unless
+    // FLBM_ROW_PAIRS=0; the same bits either way
+    e->np = row_pairs_enabled() ? 2 : 1;
     const int occ = occupancy(e, threads, smem);
     if (occ < 1) return efail(e, FLBM_E_INVALID, "tuning does not fit the device");
     const int per_sm = std::min(occ, int(t.ctas_per_sm));
@@ -204,8 +208,8 @@ cudaError_t launch_one(flbm_ensemble *e, int64_t t)
     const int every = e->p0.stats_every;
     const bool stats = every > 0 && t % every == 0;
     cudaError_t err = e->p0.precision == FLBM_FP32
-        ? launch_ens_step_f32(e->args, e->p0.scheme, odd, stats, e->grid, e->threads, e->smem, e->stream)
-        : launch_ens_step_f16(e->args, e->p0.scheme, odd, stats, e->grid, e->threads, e->smem, e->stream);
+        ? launch_ens_step_f32(e->args, e->p0.scheme, odd, stats, e->grid, e->threads, e->smem, e->stream, e->np)
+        : launch_ens_step_f16(e->args, e->p0.scheme, odd, stats, e->grid, e->threads, e->smem, e->stream, e->np);
     if (err != cudaSuccess) return err;
     return launch_ens_post(e->args, stats, uint32_t(e->tune.compute_warps), e->done(), e->dstep(), e->stream);
 }

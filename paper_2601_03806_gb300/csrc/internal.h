@@ -113,16 +113,27 @@ __host__ __device__ inline void ens_chunk(uint64_t nitems, uint32_t b, uint32_t 
     end = begin + k + (uint64_t(b) < rem ? 1u : 0u);
 }
 
-// Launchers (ens_f32.cu, ens_f16.cu): the step kernel with `threads` threads
-// (compute warps + one copy warp) and `smem` dynamic shared bytes, and its
-// resident CTAs per SM (0 if the shape does not fit; also sets the kernels'
-// shared-memory attribute on the current device).
+// Launchers (ens_f32.cu, ens_f16.cu; the two-node kernels in ens_f32p.cu,
+// ens_f16p.cu): the step kernel with np nodes per compute thread, `threads`
+// threads (compute warps + one copy warp) and `smem` dynamic shared bytes,
+// and its resident CTAs per SM (0 if the shape does not fit; also sets the
+// kernels' shared-memory attribute on the current device).
 cudaError_t launch_ens_step_f32(const EnsArgs &a, int scheme, bool odd, bool stats, int grid,
-                                int threads, size_t smem, cudaStream_t s);
+                                int threads, size_t smem, cudaStream_t s, int np);
 cudaError_t launch_ens_step_f16(const EnsArgs &a, int scheme, bool odd, bool stats, int grid,
-                                int threads, size_t smem, cudaStream_t s);
-int ens_occupancy_f32(int scheme, int threads, size_t smem);
-int ens_occupancy_f16(int scheme, int threads, size_t smem);
+                                int threads, size_t smem, cudaStream_t s, int np);
+int ens_occupancy_f32(int scheme, int threads, size_t smem, int np);
+int ens_occupancy_f16(int scheme, int threads, size_t smem, int np);
+cudaError_t launch_ens_step_f32p(const EnsArgs &a, int scheme, bool odd, bool stats, int grid,
+                                 int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_ens_step_f16p(const EnsArgs &a, int scheme, bool odd, bool stats, int grid,
+                                 int threads, size_t smem, cudaStream_t s);
+int ens_occupancy_f32p(int scheme, int threads, size_t smem);
+int ens_occupancy_f16p(int scheme, int threads, size_t smem);
+// Whether the two-node row and ensemble kernels serve FP32 / FP16 storage:
+// FLBM_ROW_PAIRS=0 (environment, read at every call) keeps one node per
+// thread (a measuring knob; the default is two).  Both give the same bits.
+bool row_pairs_enabled();
 // After each ensemble step: per-replica FP64 totals of the partial slots into
 // each replica's DevStats (stats steps), then the step counter advances.
 cudaError_t launch_ens_post(const EnsArgs &a, bool stats, uint32_t cwarps, unsigned int *done,

@@ -42,7 +42,6 @@
 
 #include <cuda_fp16.h>
 
-#include <cstdlib>
 #include <type_traits>
 
 #include "internal.h"
@@ -1036,15 +1035,6 @@ __global__ void __launch_bounds__(NP == 2 ? kRowPairCompute + 32 : kRowCompute +
 
 // Dynamic shared memory of a row-pipeline CTA at most.
 constexpr size_t kRowMaxSmem = 200 * 1024;
-
-// Whether the two-node row kernel may serve FP32 / FP16 storage:
-// FLBM_ROW_PAIRS=0 (environment, read at every launch) keeps one node per
-// thread (a measuring knob; the default is two).  Both give the same bits.
-inline bool row_pairs_enabled()
-{
-    const char *e = std::getenv("FLBM_ROW_PAIRS");
-    return !(e && std::atoi(e) == 0);
-}
 
 // Whether the row pipeline serves a box of row length nx, and its CTA shape:
 // np nodes per compute thread, 1 << stages_log2 shared-memory stages.
