@@ -43,9 +43,11 @@ BYTES_PER_NODE = {"fp32": 27 * 4 * 2, "fp16": 27 * 2 * 2, "fp64": 27 * 8 * 2}
 CS2 = 1.0 / 3.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_rows_f32_gmf_traffic.txt")
 KERNEL_SOURCES = ["step_kernel.cuh", "lattice.cuh", "internal.h", "step_f32.cu"]
+TRAFFIC16_FILE = os.path.join(ROOT, "profiles", "k_step_rows_f16_gmf_traffic.txt")
+KERNEL16_SOURCES = ["step_kernel.cuh", "lattice.cuh", "internal.h", "step_f16.cu"]
 ENS_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_ens_f32_gmf_traffic.txt")
 ENS_KERNEL_SOURCES = ["ens_kernel.cuh", "step_kernel.cuh", "lattice.cuh", "internal.h", "stats.cuh",
-                      "ens_f32.cu"]
+                      "ens_f32.cu", "ens_f32p.cu"]
 LEARNED_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_learned_f32_traffic.txt")
 MS_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_ms_step_f32_gmf_traffic.txt")
 MS_KERNEL_SOURCES = ["mstate.cu", "step_kernel.cuh", "lattice.cuh", "internal.h"]
@@ -457,11 +459,18 @@ def run_ours(args, rank, local, ws):
     peak, peak_src = measured_hbm_peak()
     node_bytes = MS_BYTES_PER_NODE if moments else BYTES_PER_NODE[args.precision]
     achieved = node_bytes * N / (k_ms / 1e3) / 1e9
-    traffic = recorded_traffic(N) if args.precision == "fp32" else None
+    traffic = {"fp32": recorded_traffic(N),
+               "fp16": recorded_traffic(N, TRAFFIC16_FILE, KERNEL16_SOURCES)}.get(args.precision)
     rows_path = nx % 32 == 0 and 2 * 27 * nx * es <= 200 * 1024 and os.environ.get("FLBM_ROWS", "1") != "0"
+    # two nodes per thread for FP32 / FP16 rows of 256 and more (FLBM_ROW_PAIRS=0: one)
+    pairs = (args.precision != "fp64" and nx >= 256 and 2 * 27 * nx * es <= 2 * 27 * 512 * 4
+             and os.environ.get("FLBM_ROW_PAIRS", "1") != "0")
     st_name = {"fp32": "float", "fp16": "__half", "fp64": "double"}[args.precision]
-    kname = ("flbm::k_step_rows<%s,GMF,*,stats> (TMA row pipeline)" % st_name if rows_path
-             else "flbm::k_step<%s,GMF,*,stats> (direct)" % st_name)
+    kname = ("flbm::k_step_rows<%s,GMF,*,stats,NP=%d> (TMA row pipeline, %s)"
+             % (st_name, 2 if pairs else 1, "two nodes per thread" if pairs else "one node per thread")
+             if rows_path else "flbm::k_step<%s,GMF,*,stats> (direct)" % st_name)
+    if rows_path and not pairs:
+        traffic = None     # the records are of the two-node kernel
     if not rows_path:
         traffic = None
     if moments:
@@ -651,8 +660,8 @@ def run_ensemble(args, rank, local, ws):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
                 "traffic": recorded_traffic(N, ENS_TRAFFIC_FILE, ENS_KERNEL_SOURCES),
-                "kernel": "flbm::k_step_ens<float,float,GMF,*,stats> + flbm::k_ens_post (per-step "
-                          "time of both, graph replay)",
+                "kernel": "flbm::k_step_ens<float,float,GMF,*,stats,NP=%d> + flbm::k_ens_post (per-step "
+                          "time of both, graph replay)" % (1 if os.environ.get("FLBM_ROW_PAIRS", "1") == "0" else 2),
                 "kernel_ms": step_ms, "algorithmic_bytes_per_launch": BYTES_PER_NODE["fp32"] * N}
 
     # statistics run (config 4: 5000 steps): ensemble-averaged <u_a^2> of
