@@ -153,16 +153,26 @@ size_t flbm_state_bytes(const flbm_params *p);
 
 /* Create a context with flbm_params_init defaults: FP32 deviations, AA in
  * place, library-owned memory and stream; state f_i = w_i rho0 at step 0.
- * out receives the context (NULL on failure). */
+ * The arguments are the run parameters of the paper's equilibrium-
+ * fluctuation tests (Sec. III): a periodic nx x ny x nz box, the relaxation
+ * time tau of the BGK collision (Sec. II: omega = 1/tau, shear viscosity
+ * c_s^2 (tau - 1/2), tau > 1/2), the thermal energy kT of the fluctuation-
+ * dissipation amplitudes (Eqs. fluct_phi, fluct_phig), the reference density
+ * rho0, the key of the noise generator, and the scheme compared in Sec. III
+ * (BGK-, GMF- or Reg-FLBM).  out receives the context (NULL on failure);
+ * FLBM_E_INVALID on out-of-range parameters, FLBM_E_NOMEM / FLBM_E_CUDA when
+ * the device allocation or set-up fails. */
 int flbm_create(int nx, int ny, int nz, double tau, double kT, double rho0,
                 uint64_t seed, int scheme, flbm_ctx **out);
 
-/* Create from explicit parameters.  dev_buf: NULL, or a device buffer of at
- * least flbm_state_bytes(p) bytes, 256-byte aligned, that the caller (e.g.
- * PyTorch) owns and keeps alive; cuda_stream: NULL for a library-owned
- * stream, else a cudaStream_t on the current device that all work of this
- * context is ordered on.  FLBM_E_INVALID if dev_buf is not device (or
- * managed) memory. */
+/* Create from explicit parameters (the Sec. III run parameters of
+ * flbm_create, plus storage precision, noise density reading, reduction
+ * cadence, noise stream and state form; see flbm_params).  dev_buf: NULL, or
+ * a device buffer of at least flbm_state_bytes(p) bytes, 256-byte aligned,
+ * that the caller (e.g. PyTorch) owns and keeps alive; cuda_stream: NULL for
+ * a library-owned stream, else a cudaStream_t on the current device that all
+ * work of this context is ordered on.  FLBM_E_INVALID if dev_buf is not
+ * device (or managed) memory or a parameter is out of range. */
 int flbm_create_ex(const flbm_params *p, void *dev_buf, size_t dev_bytes,
                    void *cuda_stream, flbm_ctx **out);
 
