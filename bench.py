@@ -14,7 +14,9 @@ Extra lines (not the default): ``--precision fp16`` (FP16 storage),
 ``--state-form moments`` (the thread-safe moment-state form, ten numbers per
 node), ``--workload ensemble`` (328 replica boxes in one persistent kernel
 per step) and ``--workload learned`` (GMF-FLBM plus the tensor-core network
-correction on 256^3, with its training and a statistics run).
+correction on 256^3, with its training and a statistics run).  The default
+line also carries brief timings of these workloads under ``variants``
+(single GPU only; ``--no-variants`` skips them).
 
 Multi-GPU: the path runs independent replica boxes, one per rank ("replicas
 only", weak scaling); torch.distributed is used for the barrier and the
@@ -71,6 +73,9 @@ def parse_args(argv=None):
                     help="box: what the box keeps between steps (moments: the thread-safe form, "
                          "ten FP32 numbers per node, FP32 GMF only)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="box: skip the brief timings of the extra workloads (FP16 storage, moment "
+                         "state, ensemble, learned step) that the default line reports under 'variants'")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", choices=["box", "ensemble", "learned"], default="box",
                     help="box: one 512^3 box (default); ensemble: 256 x 32^3 + 64 x 64^3 + "
@@ -566,9 +571,86 @@ def run_ours(args, rank, local, ws):
                      "start_offset": mass0 / (N * rho0) - 1.0,
                      "start_offset_sd": (3.0 * N * rho0 * kT) ** 0.5 / (N * rho0)},
         }
-        print(json.dumps(line), flush=True)
     lat.close()
+    if rank == 0:
+        default_box = (nx, ny, nz) == (512, 512, 512) and args.precision == "fp32" and not moments
+        if ws == 1 and default_box and not args.no_variants:
+            torch.cuda.empty_cache()
+            line["variants"] = measure_variants(args, flbm, torch, stream, gpu_id)
+        print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_variants(args, flbm, torch, stream, gpu_id):
+    """Brief timings, in the process of the default line, of the extra
+    workloads (their own lines give the full reports): FP16 storage and the
+    moment-state form on the 512^3 box, the config-4 ensemble in the launch
+    shape its autotuner picks (items 512, 2 stages, 4 compute warps, 2 CTAs
+    per SM), and the learned step on 256^3 with an untrained network (the
+    kernel's work does not depend on the weights) beside plain GMF on the
+    same box.  Each: warm-up, then args.steps steps between CUDA events on
+    the library's stream; MLUPS and the fraction of the measured HBM copy
+    rate at its algorithmic bytes."""
+    import numpy as np
+    tau, kT, rho0, seed = WORKLOAD["tau"], WORKLOAD["kT"], WORKLOAD["rho0"], WORKLOAD["seed"]
+    peak, _ = measured_hbm_peak()
+
+    def timed(step, nodes, node_bytes):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        step(args.steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        return {"value": nodes / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
+                "roofline_frac": node_bytes * nodes / (ms / 1e3) / 1e9 / peak}
+
+    def box(n, prec, node_bytes, what, state_form=flbm.FLBM_STATE_POPULATIONS, scheme=flbm.FLBM_GMF,
+            t=tau, mlp=None):
+        lat = flbm.Lattice(n, n, n, t, kT, rho0=rho0, seed=seed, scheme=scheme, precision=prec,
+                           stats_every=1, torch_memory=True, stream=stream, state_form=state_form)
+        try:
+            if mlp is not None:
+                lat.set_mlp(mlp)
+            lat.init_thermal(seed)
+            lat.step(args.warmup)
+            r = timed(lat.step, n ** 3, node_bytes)
+        finally:
+            lat.close()
+        r["what"] = what
+        return r
+
+    out = {}
+    with ClockSampler(gpu_id) as clk:
+        out["fp16_storage"] = box(512, flbm.FLBM_FP16, BYTES_PER_NODE["fp16"],
+                                  "512^3 GMF, FP16 deviation storage, FP32 arithmetic (108 B/node)")
+        torch.cuda.empty_cache()
+        out["moment_state"] = box(512, flbm.FLBM_FP32, MS_BYTES_PER_NODE,
+                                  "512^3 GMF, moment-state form (80 B/node)",
+                                  state_form=flbm.FLBM_STATE_MOMENTS)
+        torch.cuda.empty_cache()
+        ens = flbm.Ensemble(ensemble_params(flbm, seed), stream=stream)
+        try:
+            ens.set_tuning(512, 2, 4, 2)
+            for r, rep in enumerate(ens.replicas):
+                rep.init_thermal(seed * 1000 + r)
+            ens.step(args.warmup + (args.warmup % 2))
+            out["ensemble"] = timed(ens.step, ens.nodes, BYTES_PER_NODE["fp32"])
+            out["ensemble"]["what"] = ("256 x 32^3 + 64 x 64^3 + 8 x 128^3 GMF replicas, one persistent "
+                                       "kernel + one statistics kernel per step, graph replay")
+        finally:
+            ens.close()
+        torch.cuda.empty_cache()
+        mlp = (0.05 * np.random.default_rng(1).standard_normal(flbm.MLP_NPARAM)).astype(np.float32)
+        out["learned"] = box(256, flbm.FLBM_FP32, BYTES_PER_NODE["fp32"],
+                             "256^3 learned collision (GMF + tcgen05 network correction), tau 0.8",
+                             scheme=flbm.FLBM_LEARNED, t=0.8, mlp=mlp)
+        out["plain_256"] = box(256, flbm.FLBM_FP32, BYTES_PER_NODE["fp32"],
+                               "256^3 plain GMF, tau 0.8 (the learned step's reference)", t=0.8)
+    out["clocks"] = clk.summary()
+    return out
 
 
 # ----------------------------------------------------------------------------
