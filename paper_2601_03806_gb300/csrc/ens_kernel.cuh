@@ -12,13 +12,16 @@
 // the 27 plane segments of the item between HBM and a shared-memory stage
 // with bulk copies (cp.async.bulk) completing on a "full" mbarrier; the
 // compute warps apply the periodic x-shift in shared memory, collide
-// (collide_core, the same code as the single-box kernels), overwrite the
+// (collide_core, the same code as the single-box kernels, so a replica's
+// populations equal its single box's bit for bit; with NP = 2 a thread
+// collides two adjacent nodes of a row at once), overwrite the
 // segments and release the stage through an "empty" mbarrier, after which
 // the copy warp stores the segments back.  In the odd AA form a segment that
 // starts or ends on the periodic y-seam of the plane takes two copies.
 //
-// Statistics: each compute warp keeps FP32 per-thread sums of the replica
-// it is on and, when the CTA leaves that replica, writes its warp totals to
+// Statistics: each compute warp keeps FP32 per-thread sums (per lane with
+// NP = 2) of the replica it is on and, when the CTA leaves that replica,
+// writes its warp totals to
 // partial slot (cta + replica, warp); along the chunk order the pairs
 // (cta, replica) met are distinct, so slot cta + replica is unique.  No
 // barrier is involved, so a wait that runs out cannot hang the others.  The

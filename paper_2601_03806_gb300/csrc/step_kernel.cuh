@@ -9,7 +9,11 @@
 // Both forms realise f_i(x + c_i, t+1) = f*_i(x, t) (LHS of Eq. flbe2) on a
 // periodic box, and the set of locations a node reads is the set it writes.
 //
-// Per node (Eq. flbe2 in mode space), collide_core:
+// Per node (Eq. flbe2 in mode space), collide_core (collide_modes +
+// noise_synthesise), on one node (lane type float or double) or on two nodes
+// at once (float2, one node per lane, as packed FP32 instructions); every
+// operation is one explicitly rounded IEEE operation, so every kernel gives
+// the same bits:
 //   a2  forward Hermite projection (three 1-D passes): drho, j_a, m_ab
 //   a3  a2neq_ab = m_ab - rho u_a u_b (equal to Eq. moments2 because the
 //       second-order f^eq has second Hermite moment rho u_a u_b)
@@ -20,7 +24,8 @@
 //       Philox4x32-10 keyed on (seed; node, step, block | stream << 8) +
 //       Box-Muller
 //   a7  f*_i = w_i sum_k e_ki M_k / b_k (three 1-D passes), minus w_i rho0
-//   a9  optional per-thread partial sums for the FP64 reductions
+//   a9  optional per-thread partial sums of the reductions, folded per warp
+//       every 8 rows into exact (hi, lo) slots and summed per CTA in FP64
 //
 // Two kernels move the data (a1 load, a8 store):
 //   k_step_rows  (rows whose x-extent is a multiple of 32 and fits shared
@@ -29,13 +34,15 @@
 //                plane segments the row reads -- from the 9 neighbouring rows
 //                in the odd form -- into shared memory with TMA bulk copies
 //                (cp.async.bulk, one lane per segment) completing on a "full"
-//                mbarrier, two rows ahead of the compute warps.  The compute
+//                mbarrier, stages ahead of the compute warps.  The compute
 //                warps apply the periodic +-1 x-shift inside shared memory,
 //                collide, overwrite the same segments (a node's read set is
 //                its write set) and release the stage on an "empty"
 //                mbarrier; the producer then bulk-stores the segments back.
 //                All HBM traffic is aligned bulk transfers and no CTA-wide
-//                barrier sits in the loop.
+//                barrier sits in the loop.  FP32 / FP16 rows of 256 nodes
+//                and more: a compute thread collides two adjacent nodes at
+//                once (NP = 2); otherwise one (NP = 1).
 //   k_step       (any box): one thread per node, a CTA per 128-node chunk of
 //                a row, direct coalesced loads and stores.
 #pragma once
