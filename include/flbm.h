@@ -205,6 +205,16 @@ int flbm_stats_reset(flbm_ctx *c);
 int flbm_structure_factor(flbm_ctx *c, int observable, int nshell, double *S,
                           int64_t *count);
 
+/* Spectral equilibration ratio of one observable of the current state (Sec.
+ * III): ER_m(|k|) = S_m(|k|) / S_m^th with S_m as flbm_structure_factor
+ * returns it and S_m^th the flat value of the lattice invariant measure per
+ * node, (3, 3, 5, 1) rho0 kT for rho, sum_a j_a, sum_a Pi_aa, sum_{a<b}
+ * Pi_ab and rho0 kT for each momentum component.  er[s] and count[s] for
+ * shells s < nshell (er[s] = 0 for an empty shell).  FLBM_E_INVALID when
+ * kT = 0 (no fluctuations to compare) and for the arguments
+ * flbm_structure_factor rejects. */
+int flbm_spectral_er(flbm_ctx *c, int observable, int nshell, double *er, int64_t *count);
+
 /* Absolute populations f_i(x, t) of the current step, FP64, SoA f[i*N+n]. */
 int flbm_get_populations(flbm_ctx *c, double *f);
 int flbm_set_populations(flbm_ctx *c, const double *f);

@@ -9,8 +9,9 @@
 * The min/max of ER_m over the shells |n| in [4, 64] (Fig. 2), shells being
   integer wavevector radii round(|n|).
 
-Only host-side arithmetic on the spectra happens here; the spectra come from
-the CUDA path (cuFFT + FP64 shell sums).
+The per-snapshot ratio comes from the C ABI (flbm_spectral_er: the CUDA
+path's cuFFT spectrum and FP64 shell sums over S_m^th); here the snapshots
+are averaged and the window extrema taken.
 """
 from __future__ import annotations
 
@@ -40,16 +41,15 @@ def er_spectrum(lat, nshell: int, snapshots: int, every: int,
                 observables=PAPER_OBSERVABLES):
     """Advance `lat` by `every` steps `snapshots` times and return
     {observable: (ER_m per shell, shell populations)} of the snapshot average."""
-    rho0, kT = lat.params.rho0, lat.params.kT
     acc = {m: np.zeros(nshell) for m in observables}
     cnt = {}
     for _ in range(snapshots):
         lat.step(every)
         for m in observables:
-            S, c = lat.structure_factor(m, nshell)
-            acc[m] += S
+            er, c = lat.spectral_er(m, nshell)
+            acc[m] += er
             cnt[m] = c
-    return {m: (acc[m] / snapshots / theory(m, rho0, kT), cnt[m]) for m in observables}
+    return {m: (acc[m] / snapshots, cnt[m]) for m in observables}
 
 
 def window_extrema(er, counts, kmin: int = 4, kmax: int = 64):

@@ -657,6 +657,20 @@ int flbm_structure_factor(flbm_ctx *c, int observable, int nshell, double *S, in
     return FLBM_OK;
 }
 
+int flbm_spectral_er(flbm_ctx *c, int observable, int nshell, double *er, int64_t *count)
+{
+    if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
+    if (!(c->p.kT > 0.0)) return fail(c, FLBM_E_INVALID, "the spectral ER needs kT > 0");
+    const int rc = flbm_structure_factor(c, observable, nshell, er, count);
+    if (rc != FLBM_OK) return rc;
+    // flat S_m^th of the lattice invariant measure <dg_i dg_j> = (rho0 kT /
+    // c_s^2) w_i delta_ij, per node
+    static const double factor[7] = {3.0, 3.0, 5.0, 1.0, 1.0, 1.0, 1.0};
+    const double th = factor[observable] * c->p.rho0 * c->p.kT;
+    for (int s = 0; s < nshell; ++s) er[s] = count[s] > 0 ? er[s] / th : 0.0;
+    return FLBM_OK;
+}
+
 int flbm_get_populations(flbm_ctx *c, double *f)
 {
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");

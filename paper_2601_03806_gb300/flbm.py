@@ -81,6 +81,7 @@ def _load():
         "flbm_stats": ([vp, P(flbm_stats_t)], i32),
         "flbm_stats_reset": ([vp], i32),
         "flbm_structure_factor": ([vp, i32, i32, vp, vp], i32),
+        "flbm_spectral_er": ([vp, i32, i32, vp, vp], i32),
         "flbm_get_populations": ([vp, vp], i32),
         "flbm_set_populations": ([vp, vp], i32),
         "flbm_probe": ([vp, vp, i64, vp], i32),
@@ -131,6 +132,7 @@ flbm_moments = lib.flbm_moments
 flbm_stats = lib.flbm_stats
 flbm_stats_reset = lib.flbm_stats_reset
 flbm_structure_factor = lib.flbm_structure_factor
+flbm_spectral_er = lib.flbm_spectral_er
 flbm_get_populations = lib.flbm_get_populations
 flbm_set_populations = lib.flbm_set_populations
 flbm_probe = lib.flbm_probe
@@ -287,6 +289,14 @@ class _CtxOps:
         cnt = np.zeros(nshell, np.int64)
         self._check(lib.flbm_structure_factor(self._h, int(observable), int(nshell), _ptr(S), _ptr(cnt)))
         return S, cnt
+
+    def spectral_er(self, observable: int, nshell: int):
+        """ER_m per shell of the current state and the shell populations
+        (see flbm_spectral_er)."""
+        er = np.zeros(nshell)
+        cnt = np.zeros(nshell, np.int64)
+        self._check(lib.flbm_spectral_er(self._h, int(observable), int(nshell), _ptr(er), _ptr(cnt)))
+        return er, cnt
 
     def get_populations(self) -> np.ndarray:
         f = np.empty((Q, self.nz, self.ny, self.nx))

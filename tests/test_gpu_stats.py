@@ -209,3 +209,27 @@ def test_smallest_viscosity_bgk_fails_gmf_and_reg_hold(F, oracle_mod):
         assert 0.85 < lo and hi < 1.3, (m, lo, hi)
         sel = slice(4, 21)
         assert np.abs(er_g[sel] - er_r[sel]).max() < 0.01, (m, er_g[sel], er_r[sel])
+
+
+def test_spectral_er_abi(F):
+    """flbm_spectral_er returns flbm_structure_factor's S_m(|k|) over the flat
+    invariant-measure value (3, 3, 5, 1, 1, 1, 1) rho0 kT of each observable,
+    and rejects kT = 0."""
+    n, kT, rho0 = 32, 1e-4, 1.3
+    g = F.Lattice(n, n, n, 0.8, kT, rho0=rho0, seed=5, precision=1)
+    g.init_thermal(6)
+    g.step(10)
+    th = np.array([3, 3, 5, 1, 1, 1, 1]) * rho0 * kT
+    for obs in range(7):
+        er, cnt = g.spectral_er(obs, 24)
+        S, cnt2 = g.structure_factor(obs, 24)
+        assert np.array_equal(cnt, cnt2)
+        assert np.allclose(er[cnt > 0], S[cnt > 0] / th[obs], rtol=1e-15, atol=0)
+        assert np.all(er[cnt == 0] == 0)
+        assert abs(er[2:16].mean() - 1) < 0.1          # a thermal sample: flat, near 1
+    g.close()
+    z = F.Lattice(8, 8, 8, 0.8, 0.0, precision=1)
+    with pytest.raises(F.FlbmError) as ei:
+        z.spectral_er(0, 8)
+    assert ei.value.code == F.FLBM_E_INVALID
+    z.close()
