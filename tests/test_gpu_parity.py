@@ -294,7 +294,10 @@ def test_full_size_sampled_nodes(F, O):
 
 
 @pytest.mark.parametrize("scheme", [0, 1, 2])
-@pytest.mark.parametrize("shape", [(32, 3, 2), (64, 5, 4), (96, 2, 1), (32, 1, 1), (64, 1, 2)])
+@pytest.mark.parametrize("shape", [(32, 3, 2), (64, 5, 4), (96, 2, 1), (32, 1, 1), (64, 1, 2),
+                                   # two nodes per thread (FP32 / FP16 rows of 256 and more):
+                                   # degenerate neighbourhoods, and 144 pairs over 96 threads
+                                   (256, 1, 1), (256, 2, 1), (512, 1, 2), (288, 3, 2)])
 def test_row_pipeline_parity(F, O, scheme, shape):
     nx, ny, nz = shape
     f0 = perturbed(O, nx, ny, nz, seed=ny * 7 + nz, amp=0.02)
