@@ -252,13 +252,19 @@ def test_structure_factor_parity(F, O, precision, rtol):
 
 
 # ---------------------------------------------------------------------------
-# Full-size launch configuration of the benchmark (512^3 FP32 GMF, tau=0.6,
-# kT=1e-5): sampled nodes checked one by one against the oracle's collision.
+# Full-size launch configuration of the benchmark (512^3 GMF, tau=0.6,
+# kT=1e-5; FP32 storage, and the FP16 storage variant): sampled nodes checked
+# one by one against the oracle's collision of the probed inputs.
 
 
-def test_full_size_sampled_nodes(F, O):
+# mom_tol: total momentum starts at 0 and the collision conserves it; what
+# remains is storage rounding: about 1e-10 per node and step in FP32, about
+# 2e-6 in FP16 (half ulp of deviations of ~3e-3), random-walking over N =
+# 1.3e8 nodes and 4 steps to ~2e-6 (FP32) and ~0.05 (FP16)
+@pytest.mark.parametrize("precision,tol,mom_tol", [(1, 2e-6, 1e-3), (2, 2e-5, 0.2)])
+def test_full_size_sampled_nodes(F, O, precision, tol, mom_tol):
     n, tau, kT, seed = 512, 0.6, 1e-5, 2024
-    g = gpu(F, n, n, n, tau, kT, seed=seed, precision=1)
+    g = gpu(F, n, n, n, tau, kT, seed=seed, precision=precision)
     T = O.tables()
     c = T["c"]
     rng = np.random.default_rng(0)
@@ -281,10 +287,10 @@ def test_full_size_sampled_nodes(F, O):
             for i in range(27):
                 fs = O.collide_node(1, tau, kT, fin[p * 27 + i], seed=seed,
                                     node=int(src[p * 27 + i]), step=t_check)
-                assert abs(fout[p, i] - fs[i]) < 2e-6, (p, i, fout[p, i], fs[i])
+                assert abs(fout[p, i] - fs[i]) < tol, (p, i, fout[p, i], fs[i])
     s = g.stats()
     assert abs(s["mass"] / n ** 3 - 1) < 1e-9
-    assert np.abs(s["mom"]).max() < 1e-3
+    assert np.abs(s["mom"]).max() < mom_tol
 
 
 # ---------------------------------------------------------------------------
