@@ -17,15 +17,18 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
                         uniform-flow equilibrium fixed point at every tau and the
                         post-collision second and ghost moments of a moving state
                         (the f^eq subtraction of Eq. moments2)
-* ``REG`` scheme        parity unpinned for its ghost relaxation (the paper does
-                        not define Reg-FLBM's ghost non-equilibrium treatment);
-                        its full-order equilibrium coefficients are pinned against
-                        the product-form D3Q27 equilibrium
+* ``REG`` scheme        follows a reading (the paper does not define Reg-FLBM's
+                        ghost non-equilibrium treatment: full-order Maxwellian
+                        coefficients, unit ghost relaxation); the implementation of
+                        that reading is pinned: tau = 1 map to the product-form
+                        D3Q27 equilibrium, kT = 0 ghost coefficients rho u^deg and
+                        relaxed second moment at tau = 0.6, 2, the uniform-flow
+                        fixed point, and the AR(1) ghost statistics
 * ``structure_factor``  pinned: numpy FFT, Parseval, single-plane-wave shell
 * ``mlp`` (learned collision): forward/backward pinned by central finite
                         differences and closed forms, the projection by the
                         conservation identities, the training target by the
                         closed-form ghost synthesis; the target inherits the
-                        Reg-FLBM reading (parity unpinned against the paper)
+                        Reg-FLBM reading (not checkable against the paper's text)
 """
 from .oracle import *  # noqa: F401,F403

@@ -25,7 +25,8 @@ equilibrium content w_i sum_{k >= 10} e_ki rho u^(deg k) / b_k.
 Parity status: ``forward``/``backward`` pinned by central finite differences
 and closed forms; ``project`` by the conservation identities; ``target`` by
 the closed-form ghost synthesis from the Table II basis (it inherits the
-Reg-FLBM reading, which is itself parity unpinned against the paper).
+Reg-FLBM reading, whose implementation is pinned but which the paper's text
+does not define).
 
 Parameter vector (float, this order): W1[64][28], b1[64], W2[64][64],
 b2[64], W3[27][64], b3[27] -- 7771 values.
