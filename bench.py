@@ -46,7 +46,7 @@ CS2 = 1.0 / 3.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_rows_f32_gmf_traffic.txt")
 KERNEL_SOURCES = ["step_kernel.cuh", "lattice.cuh", "internal.h", "step_f32.cu"]
 TRAFFIC16_FILE = os.path.join(ROOT, "profiles", "k_step_rows_f16_gmf_traffic.txt")
-KERNEL16_SOURCES = ["step_kernel.cuh", "lattice.cuh", "internal.h", "step_f16.cu"]
+KERNEL16_SOURCES = ["step_kernel.cuh", "lattice.cuh", "internal.h", "step_f16.cu", "step_f16_nx512.cu"]
 ENS_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_ens_f32_gmf_traffic.txt")
 ENS_KERNEL_SOURCES = ["ens_kernel.cuh", "step_kernel.cuh", "lattice.cuh", "internal.h", "stats.cuh",
                       "ens_f32.cu", "ens_f32p.cu"]
@@ -471,11 +471,16 @@ def run_ours(args, rank, local, ws):
     pairs = (args.precision != "fp64" and nx >= 256 and 2 * 27 * nx * es <= 2 * 27 * 512 * 4
              and os.environ.get("FLBM_ROW_PAIRS", "1") != "0")
     st_name = {"fp32": "float", "fp16": "__half", "fp64": "double"}[args.precision]
-    kname = ("flbm::k_step_rows<%s,GMF,*,stats,NP=%d> (TMA row pipeline, %s)"
-             % (st_name, 2 if pairs else 1, "two nodes per thread" if pairs else "one node per thread")
+    # FP16 rows of exactly 512 nodes run the kernel with the row length fixed at compile time
+    fixed = pairs and args.precision == "fp16" and nx == 512
+    kname = ("flbm::k_step_rows<%s,GMF,*,stats,NP=%d%s> (TMA row pipeline, %s)"
+             % (st_name, 2 if pairs else 1, ",NXC=512" if fixed else "",
+                "two nodes per thread" if pairs else "one node per thread")
              if rows_path else "flbm::k_step<%s,GMF,*,stats> (direct)" % st_name)
     if rows_path and not pairs:
         traffic = None     # the records are of the two-node kernel
+    if args.precision == "fp16" and not fixed:
+        traffic = None     # the FP16 record is of the fixed-length (512) kernel
     if not rows_path:
         traffic = None
     if moments:

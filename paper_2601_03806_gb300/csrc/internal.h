@@ -153,6 +153,13 @@ cudaError_t launch_step_f16(void *g, const StepArgs<float> &a, int scheme, bool 
 void step_occupancy_f64(int scheme, uint32_t nx, bool stats, int &direct, int &rows);
 void step_occupancy_f32(int scheme, uint32_t nx, uint64_t n, bool stats, int &direct, int &rows);
 void step_occupancy_f16(int scheme, uint32_t nx, uint64_t n, bool stats, int &direct, int &rows);
+// The FP16-storage two-node row kernels for rows of exactly 512 nodes
+// (step_f16_nx512.cu), which step_f16.cu calls when the row plan of the box
+// takes two nodes per thread in full CTAs.  FP32 keeps the general kernel:
+// there the step is at the HBM bound and the fixed length gains nothing.
+cudaError_t launch_rows_f16_nx512(void *g, const StepArgs<float> &a, int scheme, bool odd, bool stats,
+                                  int row_grid, cudaStream_t s);
+int rows_occupancy_f16_nx512(int scheme, bool stats);
 
 // Step constants shared by flbm_step and flbm_step_noalloc (capi.cu): the
 // Philox round keys, the density used by the noise, and the per-mode

@@ -857,11 +857,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 // while the row lands; NP = 2 (FP32 arithmetic): it collides the adjacent
 // nodes (x, x+1) at once as packed FP32 pairs, and moves each unshifted
 // segment value pair with one shared access.
-template <typename S, typename R, int SCHEME, bool ODD, bool STATS, int NP>
+// NXC = 0: the row length is a.nx.  NXC > 0 (NP = 2 only): the row length
+// is the constant NXC = a.nx and the CTA has kRowPairCompute compute
+// threads, so every segment offset in the stage is an immediate of the
+// shared-memory access instead of an address computed per access.
+template <typename S, typename R, int SCHEME, bool ODD, bool STATS, int NP, uint32_t NXC = 0>
 __global__ void __launch_bounds__(NP == 2 ? kRowPairCompute + 32 : kRowCompute + 32,
                                   NP == 2 ? row_pair_ctas<S>() : (sizeof(S) <= 4 ? 2 : 1))
     k_step_rows(S *__restrict__ g, const StepArgs<R> a, uint32_t nst_log2)
 {
+    static_assert(NXC == 0 || (NP == 2 && NXC % 32 == 0), "a fixed row length needs two nodes per thread");
     using V = typename std::conditional<NP == 2, float2, R>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kRowMaxStages], empty[kRowMaxStages];
@@ -869,8 +874,8 @@ __global__ void __launch_bounds__(NP == 2 ? kRowPairCompute + 32 : kRowCompute +
     const uint32_t nst = 1u << nst_log2, st_mask = nst - 1;
     __shared__ TotSlot<R> tot[32][NSTAT];
     S *const stage = reinterpret_cast<S *>(smem_raw);
-    const uint32_t nx = a.nx;
-    const uint32_t nc = blockDim.x - 32;                  // compute threads
+    const uint32_t nx = NXC ? NXC : a.nx;
+    const uint32_t nc = NXC ? uint32_t(kRowPairCompute) : blockDim.x - 32;   // compute threads
     const uint32_t stage_elems = uint32_t(kQ) * nx;
     const uint32_t seg_bytes = nx * uint32_t(sizeof(S));
     const uint64_t nrows = uint64_t(a.ny) * a.nz;
@@ -943,6 +948,7 @@ __global__ void __launch_bounds__(NP == 2 ? kRowPairCompute + 32 : kRowCompute +
                 break;
             }
             S *st = stage + size_t(s) * stage_elems;
+#pragma unroll 1
             for (uint32_t x = 2 * threadIdx.x; x < nx; x += 2 * nc) {
                 // periodic x-1, x, x+1 of the nodes x (lane .x) and x+1 (lane .y);
                 // x is even and nx a multiple of 32, so x+1 < nx
@@ -1131,19 +1137,61 @@ cudaError_t launch_step_t(S *g, const StepArgs<R> &a, int scheme, bool odd, bool
 // Opts the four row kernels of one variant into kRowMaxSmem bytes of dynamic
 // shared memory and returns the resident CTAs per SM of the larger
 // (reducing, odd-form) one for plan rp.
-template <typename S, typename R, int SC, int NP>
+template <typename S, typename R, int SC, int NP, uint32_t NXC = 0>
 int prepare_rows(const RowPlan &rp, bool stats)
 {
     const int dmax = int(kRowMaxSmem);
-    cudaFuncSetAttribute(k_step_rows<S, R, SC, false, false, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
-    cudaFuncSetAttribute(k_step_rows<S, R, SC, false, true, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
-    cudaFuncSetAttribute(k_step_rows<S, R, SC, true, false, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
-    cudaFuncSetAttribute(k_step_rows<S, R, SC, true, true, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, false, false, NP, NXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, false, true, NP, NXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, true, false, NP, NXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, true, true, NP, NXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
     int nb = 0;
-    const cudaError_t e =
-        stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<S, R, SC, true, true, NP>, rp.threads, rp.smem)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<S, R, SC, true, false, NP>, rp.threads, rp.smem);
+    const cudaError_t e = stats
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<S, R, SC, true, true, NP, NXC>, rp.threads, rp.smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<S, R, SC, true, false, NP, NXC>, rp.threads, rp.smem);
     return (e == cudaSuccess && nb > 0) ? nb : 0;
+}
+
+// Whether a box of row length nx runs the fixed-length two-node row kernel
+// of length NXC under plan rp (the plan it would take anyway: two nodes per
+// thread and kRowPairCompute compute threads).
+template <uint32_t NXC>
+inline bool rows_fixed(const RowPlan &rp, uint32_t nx)
+{
+    return rp.use && rp.np == 2 && nx == NXC && rp.threads == kRowPairCompute + 32;
+}
+
+// One launch of the fixed-length two-node row kernel; the caller has checked
+// rows_fixed<NXC>(row_plan<S>(a.nx), a.nx).
+template <typename S, typename R, uint32_t NXC>
+cudaError_t launch_rows_fixed(S *g, const StepArgs<R> &a, int scheme, bool odd, bool stats, int row_grid,
+                              cudaStream_t s)
+{
+    const RowPlan rp = row_plan<S>(a.nx);
+#define FLBM_LAUNCH_FIXED(SC, OD, ST) \
+    k_step_rows<S, R, SC, OD, ST, 2, NXC><<<row_grid, rp.threads, rp.smem, s>>>(g, a, rp.stages_log2)
+    if (scheme == 0) {
+        if (odd) { if (stats) FLBM_LAUNCH_FIXED(0, true, true); else FLBM_LAUNCH_FIXED(0, true, false); }
+        else     { if (stats) FLBM_LAUNCH_FIXED(0, false, true); else FLBM_LAUNCH_FIXED(0, false, false); }
+    } else if (scheme == 1) {
+        if (odd) { if (stats) FLBM_LAUNCH_FIXED(1, true, true); else FLBM_LAUNCH_FIXED(1, true, false); }
+        else     { if (stats) FLBM_LAUNCH_FIXED(1, false, true); else FLBM_LAUNCH_FIXED(1, false, false); }
+    } else {
+        if (odd) { if (stats) FLBM_LAUNCH_FIXED(2, true, true); else FLBM_LAUNCH_FIXED(2, true, false); }
+        else     { if (stats) FLBM_LAUNCH_FIXED(2, false, true); else FLBM_LAUNCH_FIXED(2, false, false); }
+    }
+#undef FLBM_LAUNCH_FIXED
+    return cudaGetLastError();
+}
+
+// prepare_rows for the fixed-length kernels of one scheme.
+template <typename S, typename R, uint32_t NXC>
+int prepare_rows_fixed(int scheme, bool stats)
+{
+    const RowPlan rp = row_plan<S>(NXC);
+    if (scheme == 0) return prepare_rows<S, R, 0, 2, NXC>(rp, stats);
+    if (scheme == 1) return prepare_rows<S, R, 1, 2, NXC>(rp, stats);
+    return prepare_rows<S, R, 2, 2, NXC>(rp, stats);
 }
 
 // Resident CTAs per SM of the larger (reducing, odd-form) variant of each

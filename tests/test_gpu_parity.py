@@ -323,7 +323,8 @@ def test_row_pipeline_parity(F, O, scheme, shape):
 @pytest.mark.parametrize("shape", [(64, 6, 5), (256, 3, 2), (512, 3, 2)])
 def test_row_pipeline_matches_direct_kernel(F, O, precision, shape, scheme, monkeypatch):
     """Same inputs through the TMA row pipeline with two nodes per thread
-    (packed FP32 pairs; rows of 256 and more in FP32 / FP16), with one node
+    (packed FP32 pairs; rows of 256 and more in FP32 / FP16; rows of 512 run
+    the kernel whose row length is a compile-time constant), with one node
     per thread, and through the direct kernel (FP64 512-rows fall back to it
     in every case): identical populations, bit for bit, as every kernel runs
     the same sequence of singly rounded operations per node."""
