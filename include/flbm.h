@@ -145,10 +145,15 @@ typedef struct flbm_stats_t {
 int flbm_params_init(flbm_params *p, int nx, int ny, int nz, double tau, double kT,
                      double rho0, uint64_t seed, int scheme);
 
-/* Device bytes the population state needs (27 N elements of the storage
- * type, AA-pattern in place).  0 on invalid parameters.  A moment-state
- * context (state_form = FLBM_STATE_MOMENTS) also allocates 2 x 10 N floats
- * of its own, which dev_buf does not cover. */
+/* Device bytes of the population state (AA-pattern in place): 27 slabs of
+ * ns elements of the storage type, ns = flbm_state_bytes(p) / (27 x element
+ * size) >= N; population slot i of node n is element i ns + n.  ns is N
+ * rounded up to 64 elements plus a pad that keeps the 27 slabs from starting
+ * at addresses equal in their low bits: 1 MiB for slabs of 32 MiB and more,
+ * else none; FLBM_SLAB_PAD in the environment (bytes, a multiple of 128)
+ * sets it at any size.  0 on invalid parameters.
+ * A moment-state context (state_form = FLBM_STATE_MOMENTS) also allocates
+ * 2 x 10 N floats of its own, which dev_buf does not cover. */
 size_t flbm_state_bytes(const flbm_params *p);
 
 /* Create a context with flbm_params_init defaults: FP32 deviations, AA in
@@ -168,8 +173,10 @@ int flbm_create(int nx, int ny, int nz, double tau, double kT, double rho0,
 /* Create from explicit parameters (the Sec. III run parameters of
  * flbm_create, plus storage precision, noise density reading, reduction
  * cadence, noise stream and state form; see flbm_params).  dev_buf: NULL, or
- * a device buffer of at least flbm_state_bytes(p) bytes, 256-byte aligned,
- * that the caller (e.g. PyTorch) owns and keeps alive; cuda_stream: NULL for
+ * a device buffer, 256-byte aligned, that the caller (e.g. PyTorch) owns and
+ * keeps alive: of at least flbm_state_bytes(p) bytes (padded slabs, as
+ * described there), or of at least 27 N elements (unpadded slabs, ns = N;
+ * FLBM_E_NOMEM below that); cuda_stream: NULL for
  * a library-owned stream, else a cudaStream_t on the current device that all
  * work of this context is ordered on.  FLBM_E_INVALID if dev_buf is not
  * device (or managed) memory or a parameter is out of range. */
@@ -240,7 +247,8 @@ int flbm_probe(flbm_ctx *c, const int64_t *nodes, int64_t count, double *f);
 
 /* Raw state: deviations g_i = f_i - w_i rho0 in the storage type (double for
  * FLBM_FP64, float for FLBM_FP32, IEEE half for FLBM_FP16), SoA natural
- * layout, 27 N elements.
+ * layout, 27 N elements on the host (the device slabs' pads, see
+ * flbm_state_bytes, are left out).
  * Checkpoint = get_state + flbm_get_step; restore = set_state + set_step. */
 int flbm_get_state(flbm_ctx *c, void *host);
 int flbm_set_state(flbm_ctx *c, const void *host);

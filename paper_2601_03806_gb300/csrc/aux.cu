@@ -37,11 +37,11 @@ __device__ __forceinline__ uint64_t storage_index(int cx, int cy, int cz, uint32
 {
     if (b.parity == 0) {
         const uint64_t n = x + uint64_t(b.nx) * (y + uint64_t(b.ny) * z);
-        return uint64_t(slot_of(cx, cy, cz)) * b.n + n;
+        return uint64_t(slot_of(cx, cy, cz)) * b.ns + n;
     }
     const uint32_t xx = wrap(x, -cx, b.nx), yy = wrap(y, -cy, b.ny), zz = wrap(z, -cz, b.nz);
     const uint64_t n = xx + uint64_t(b.nx) * (yy + uint64_t(b.ny) * zz);
-    return uint64_t(slot_of(-cx, -cy, -cz)) * b.n + n;
+    return uint64_t(slot_of(-cx, -cy, -cz)) * b.ns + n;
 }
 
 // storage element <-> double
@@ -134,7 +134,7 @@ __global__ void k_scatter_f(S *g, BoxDesc b, uint64_t n0, uint64_t cn, const dou
                 for (int cz = -1; cz <= 1; ++cz) {
                     const int i = slot_of(cx, cy, cz);
                     const double w = w1(cx) * w1(cy) * w1(cz);
-                    g[uint64_t(i) * b.n + n0 + k] = from_d<S>(in[uint64_t(i) * cn + k] - w * b.rho0);
+                    g[uint64_t(i) * b.ns + n0 + k] = from_d<S>(in[uint64_t(i) * cn + k] - w * b.rho0);
                 }
     }
 }
@@ -175,7 +175,7 @@ __global__ void k_init_thermal(S *g, BoxDesc b, double kT, uint32_t key0, uint32
                     const double sw = (cx ? 0.40824829046386302 : 0.81649658092772603) *
                                       (cy ? 0.40824829046386302 : 0.81649658092772603) *
                                       (cz ? 0.40824829046386302 : 0.81649658092772603);
-                    g[uint64_t(i) * b.n + n] = from_d<S>(double(base * A(sw) * xi[i]));
+                    g[uint64_t(i) * b.ns + n] = from_d<S>(double(base * A(sw) * xi[i]));
                 }
     }
 }

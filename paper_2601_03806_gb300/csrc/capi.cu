@@ -55,6 +55,27 @@ int fail(flbm_ctx *c, int code, const std::string &msg)
 
 size_t elem_size(int prec) { return prec == FLBM_FP64 ? 8 : prec == FLBM_FP32 ? 4 : 2; }
 
+// Slab stride (elements) of the padded population storage of n nodes: slot i
+// of node n at i * ns + n, ns = n rounded up to 64 elements plus a pad of
+// kSlabPadBytes for slabs of kSlabPadFrom bytes and more, or of FLBM_SLAB_PAD
+// bytes (environment, a multiple of 128) at any size when that is set.
+// Unpadded, the 27 slabs of a 512^3 FP32 box start 2^29 bytes apart, equal in
+// every lower address bit, and the even AA step (which reads and writes the
+// same row of all 27 slabs) ran 4.6 % slower than the odd one; a 1 MB pad
+// made the step 1.0 % faster (pads of 64 KB to 12 MB: 0.8-1.0 %, 128 B:
+// 1.5 % slower).
+constexpr uint64_t kSlabPadBytes = uint64_t(1) << 20;
+constexpr uint64_t kSlabPadFrom = uint64_t(32) << 20;
+uint64_t slab_stride(uint64_t n, size_t es)
+{
+    uint64_t pad = n * es >= kSlabPadFrom ? kSlabPadBytes : 0;
+    if (const char *env = std::getenv("FLBM_SLAB_PAD")) {
+        const long long v = std::atoll(env);
+        if (v >= 0 && v % 128 == 0 && v <= (1ll << 30)) pad = uint64_t(v);
+    }
+    return (n + 63) / 64 * 64 + pad / es;
+}
+
 int prec_code(const flbm_ctx *c) { return c->p.precision == FLBM_FP64 ? 0 : (c->p.precision == FLBM_FP32 ? 1 : 2); }
 
 int parity(const flbm_ctx *c) { return int((c->step + c->phase) & 1); }
@@ -78,6 +99,7 @@ BoxDesc box_of(const flbm_ctx *c)
     b.ny = uint32_t(c->p.ny);
     b.nz = uint32_t(c->p.nz);
     b.n = c->n;
+    b.ns = c->ns;
     b.rho0 = c->p.rho0;
     b.parity = parity(c);
     return b;
@@ -173,6 +195,7 @@ StepArgs<R> make_args(const flbm_ctx *c, int64_t t)
     a.nz = uint32_t(c->p.nz);
     a.cpr = uint32_t((c->p.nx + kBlock - 1) / kBlock);
     a.n = c->n;
+    a.ns = c->ns;
     a.nchunks = uint64_t(a.cpr) * a.ny * a.nz;
     a.step = uint64_t(t);
     fill_constants_t<R>(c->p, a);
@@ -310,7 +333,11 @@ int flbm::create_ctx(const flbm_params *p, void *dev_buf, size_t dev_bytes, void
     if (!c) return fail(nullptr, FLBM_E_NOMEM, "host allocation failed");
     c->p = *p;
     c->n = uint64_t(p->nx) * uint64_t(p->ny) * uint64_t(p->nz);
-    c->g_bytes = c->n * kQ * elem_size(p->precision);
+    // padded slabs when the buffer holds them: library memory, or a dev_buf
+    // of flbm_state_bytes(p); a dev_buf of 27 N elements keeps them unpadded
+    c->ns = slab_stride(c->n, elem_size(p->precision));
+    if (dev_buf && dev_bytes < c->ns * kQ * elem_size(p->precision)) c->ns = c->n;
+    c->g_bytes = c->ns * kQ * elem_size(p->precision);
     int rc = FLBM_OK;
     auto bail = [&](int code) {
         g_create_error = c->err;
@@ -357,9 +384,9 @@ int flbm::create_ctx(const flbm_params *p, void *dev_buf, size_t dev_bytes, void
     if (p->precision == FLBM_FP64)
         step_occupancy_f64(p->scheme, uint32_t(p->nx), true, occ, occ_rows);
     else if (p->precision == FLBM_FP32)
-        step_occupancy_f32(p->scheme, uint32_t(p->nx), c->n, true, occ, occ_rows);
+        step_occupancy_f32(p->scheme, uint32_t(p->nx), c->ns, true, occ, occ_rows);
     else
-        step_occupancy_f16(p->scheme, uint32_t(p->nx), c->n, true, occ, occ_rows);
+        step_occupancy_f16(p->scheme, uint32_t(p->nx), c->ns, true, occ, occ_rows);
     step_grids(*p, c->nsm, occ, occ_rows, c->grid, c->row_grid);
     // FLBM_INJECT_STARVE=1 (environment, failure-injection tests only): the
     // row pipeline expects 16 bytes more than it copies (the learned step
@@ -384,7 +411,7 @@ int flbm::create_ctx(const flbm_params *p, void *dev_buf, size_t dev_bytes, void
     if (e == cudaSuccess) e = cudaMalloc(&c->dflags, sizeof(DevFlags));
     if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return bail(FLBM_E_NOMEM); }
     e = cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->stream);
-    if (e == cudaSuccess) e = launch_fill_rest(c->g, prec_code(c), c->n * kQ, c->stream);
+    if (e == cudaSuccess) e = launch_fill_rest(c->g, prec_code(c), c->ns * kQ, c->stream);
     if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return bail(FLBM_E_CUDA); }
     rc = reset_flags(c);
     if (rc != FLBM_OK) return bail(rc);
@@ -453,7 +480,8 @@ int flbm_params_init(flbm_params *p, int nx, int ny, int nz, double tau, double 
 size_t flbm_state_bytes(const flbm_params *p)
 {
     if (!validate_params(p).empty()) return 0;
-    return uint64_t(p->nx) * uint64_t(p->ny) * uint64_t(p->nz) * kQ * elem_size(p->precision);
+    const size_t es = elem_size(p->precision);
+    return slab_stride(uint64_t(p->nx) * uint64_t(p->ny) * uint64_t(p->nz), es) * kQ * es;
 }
 
 int flbm_create(int nx, int ny, int nz, double tau, double kT, double rho0, uint64_t seed,
@@ -789,7 +817,16 @@ int flbm_get_state(flbm_ctx *c, void *host)
     if (int rc = materialise(c)) return rc;
     const size_t es = elem_size(c->p.precision);
     if (parity(c) == 0) {
-        CK(c, cudaMemcpyAsync(host, c->g, c->g_bytes, cudaMemcpyDeviceToHost, c->stream));
+        // natural form: the host layout is the 27 slabs without their pads
+        const size_t slab = c->n * es;
+        if (c->ns == c->n) {
+            CK(c, cudaMemcpyAsync(host, c->g, kQ * slab, cudaMemcpyDeviceToHost, c->stream));
+        } else {
+            for (int i = 0; i < kQ; ++i)
+                CK(c, cudaMemcpyAsync(static_cast<char *>(host) + i * slab,
+                                      static_cast<const char *>(c->g) + i * c->ns * es, slab,
+                                      cudaMemcpyDeviceToHost, c->stream));
+        }
     } else {
         const BoxDesc b = box_of(c);
         const uint64_t N = c->n;
@@ -812,7 +849,15 @@ int flbm_set_state(flbm_ctx *c, const void *host)
     if (!c) return fail(nullptr, FLBM_E_INVALID, "ctx is NULL");
     if (!host) return fail(c, FLBM_E_INVALID, "host is NULL");
     if (int rc = replica_state_check(c)) return rc;
-    CK(c, cudaMemcpyAsync(c->g, host, c->g_bytes, cudaMemcpyHostToDevice, c->stream));
+    const size_t es = elem_size(c->p.precision), slab = c->n * es;
+    if (c->ns == c->n) {
+        CK(c, cudaMemcpyAsync(c->g, host, kQ * slab, cudaMemcpyHostToDevice, c->stream));
+    } else {
+        for (int i = 0; i < kQ; ++i)
+            CK(c, cudaMemcpyAsync(static_cast<char *>(c->g) + i * c->ns * es,
+                                  static_cast<const char *>(host) + i * slab, slab, cudaMemcpyHostToDevice,
+                                  c->stream));
+    }
     c->phase = int(c->step & 1);
     populations_written(c);
     int rc = reset_flags(c);

@@ -30,6 +30,7 @@ struct flbm_ctx {
     bool own_g = false;
     size_t g_bytes = 0;
     uint64_t n = 0;
+    uint64_t ns = 0;               // slab stride: population slot i of node n at g[i * ns + n]
     int64_t step = 0;
     int phase = 0;                 // storage is natural when ((step + phase) & 1) == 0
     uint32_t tx_pad = 0;           // failure injection into the row pipeline (tests)

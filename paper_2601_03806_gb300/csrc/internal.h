@@ -31,6 +31,7 @@ template <typename R>
 struct StepArgs {
     uint32_t nx, ny, nz, cpr;     // box; x-chunks of kBlock nodes per row
     uint64_t n;                   // nodes
+    uint64_t ns;                  // slab stride: population slot i of node n at g[i * ns + n]
     uint64_t nchunks;             // cpr * ny * nz
     uint64_t step;                // t of this collision (noise counter)
     uint32_t rk[20];              // Philox round keys (k0, k1) of rounds 0..9
@@ -148,11 +149,12 @@ cudaError_t launch_step_f32(float *g, const StepArgs<float> &a, int scheme, bool
 cudaError_t launch_step_f16(void *g, const StepArgs<float> &a, int scheme, bool odd,
                             bool stats, int grid, int row_grid, cudaStream_t s);
 // Resident CTAs per SM of the direct kernel and of the row pipeline (0 when
-// it does not serve rows of length nx) for (precision, scheme, stats); also
+// it does not serve rows of length nx) for (precision, scheme, stats; ns, the
+// slab stride, picks the index width); also
 // prepares the kernels' shared-memory attributes on the current device.
 void step_occupancy_f64(int scheme, uint32_t nx, bool stats, int &direct, int &rows);
-void step_occupancy_f32(int scheme, uint32_t nx, uint64_t n, bool stats, int &direct, int &rows);
-void step_occupancy_f16(int scheme, uint32_t nx, uint64_t n, bool stats, int &direct, int &rows);
+void step_occupancy_f32(int scheme, uint32_t nx, uint64_t ns, bool stats, int &direct, int &rows);
+void step_occupancy_f16(int scheme, uint32_t nx, uint64_t ns, bool stats, int &direct, int &rows);
 // The FP16-storage two-node row kernels for rows of exactly 512 nodes
 // (step_f16_nx512.cu), which step_f16.cu calls when the row plan of the box
 // takes two nodes per thread in full CTAs.  FP32 keeps the general kernel:
@@ -217,6 +219,7 @@ cudaError_t launch_mlp_pairs(const double *g, uint64_t cn, double rho0, double k
 struct BoxDesc {
     uint32_t nx, ny, nz;
     uint64_t n;
+    uint64_t ns;           // slab stride of the population storage (>= n)
     double rho0;
     int parity;            // 0: storage natural; 1: AA-shifted (odd form)
 };

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kBlock) k_ms_boot(const float *__restrict__ g,
     float acc[NSTAT];
 #pragma unroll
     for (int s = 0; s < NSTAT; ++s) acc[s] = 0.0f;
-    const I N = I(a.n);
+    const I N = I(a.n), NS = I(a.ns);   // moment-state stride, population slab stride
     for (uint64_t ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x) {
         const uint32_t xc = uint32_t(ch % a.cpr);
         const uint64_t r = ch / a.cpr;
@@ -129,8 +129,8 @@ __global__ void __launch_bounds__(kBlock) k_ms_boot(const float *__restrict__ g,
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     I idx;
-                    if (!ODD) idx = I(slot_of(i - 1, j - 1, k - 1)) * N + n;
-                    else idx = I(slot_of(1 - i, 1 - j, 1 - k)) * N + (nb.xs[2 - i] + nb.ry[2 - j] + nb.rz[2 - k]);
+                    if (!ODD) idx = I(slot_of(i - 1, j - 1, k - 1)) * NS + n;
+                    else idx = I(slot_of(1 - i, 1 - j, 1 - k)) * NS + (nb.xs[2 - i] + nb.ry[2 - j] + nb.rz[2 - k]);
                     v[i][j][k] = __ldcg(g + idx);
                 }
         float qm[3][3][3], rho, dj[4];
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_ms_step(const float *__restri
     float acc[NSTAT];
 #pragma unroll
     for (int s = 0; s < NSTAT; ++s) acc[s] = 0.0f;
-    const I N = I(an.n);
+    const I N = I(an.n), NS = I(an.ns);   // moment-state stride, population slab stride
     const uint32_t nx = an.nx, ny = an.ny, nz = an.nz;
     const uint32_t hx = threadIdx.x % kMsHX, hy = threadIdx.x / kMsHX;
     for (uint64_t item = blockIdx.x; item < geo.items; item += gridDim.x) {
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_ms_step(const float *__restri
 #pragma unroll
                         for (int j = 0; j < 3; ++j)
 #pragma unroll
-                            for (int k = 0; k < 3; ++k) out[I(slot_of(i - 1, j - 1, k - 1)) * N + n] = v[i][j][k];
+                            for (int k = 0; k < 3; ++k) out[I(slot_of(i - 1, j - 1, k - 1)) * NS + n] = v[i][j][k];
                 } else {
                     float qm[3][3][3], rho, dj[4];
                     collide_modes<float, SCHEME, STATS, false>(v, ac, acc, qm, rho, dj);
@@ -250,7 +250,7 @@ cudaError_t launch_ms_t(const float *ms, float *out, const StepArgs<float> &an, 
 {
     const MsGeom geo = geometry(an, zseg);
     const int g = int(std::min<uint64_t>(geo.items, uint64_t(grid)));
-    if (fits32(an.n))
+    if (fits32(an.ns))   // ns >= n: covers the 10 n moment-state indices too
         k_ms_step<SCHEME, STATS, EXPORT, uint32_t><<<g, kMsThreads, kMsRingBytes, s>>>(ms, out, an, ac, geo);
     else
         k_ms_step<SCHEME, STATS, EXPORT, uint64_t><<<g, kMsThreads, kMsRingBytes, s>>>(ms, out, an, ac, geo);
@@ -278,7 +278,7 @@ cudaError_t set_attrs()
 template <bool ODD, int SCHEME, bool STATS>
 cudaError_t launch_boot_t(const float *g, float *ms, const StepArgs<float> &a, int grid, cudaStream_t s)
 {
-    if (fits32(a.n)) k_ms_boot<ODD, SCHEME, STATS, uint32_t><<<grid, kBlock, 0, s>>>(g, ms, a);
+    if (fits32(a.ns)) k_ms_boot<ODD, SCHEME, STATS, uint32_t><<<grid, kBlock, 0, s>>>(g, ms, a);
     else k_ms_boot<ODD, SCHEME, STATS, uint64_t><<<grid, kBlock, 0, s>>>(g, ms, a);
     return cudaGetLastError();
 }

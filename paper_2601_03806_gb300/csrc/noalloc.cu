@@ -139,6 +139,7 @@ extern "C" int flbm_step_noalloc(const flbm_params *p, void *dev_state, int64_t 
     a.nz = uint32_t(p->nz);
     a.cpr = uint32_t((p->nx + kBlock - 1) / kBlock);
     a.n = n;
+    a.ns = n;   // the caller's state: 27 unpadded slabs
     a.nchunks = nchunks;
     a.step = uint64_t(step);
     fill_step_constants(*p, a);

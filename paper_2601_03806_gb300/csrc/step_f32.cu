@@ -11,14 +11,14 @@ static bool fits32(uint64_t n) { return n * kQ < (1ull << 32); }
 cudaError_t launch_step_f32(float *g, const StepArgs<float> &a, int scheme, bool odd, bool stats,
                             int grid, int row_grid, cudaStream_t s)
 {
-    if (fits32(a.n))
+    if (fits32(a.ns))
         return launch_step_t<float, float, uint32_t>(g, a, scheme, odd, stats, grid, row_grid, s);
     return launch_step_t<float, float, uint64_t>(g, a, scheme, odd, stats, grid, row_grid, s);
 }
 
-void step_occupancy_f32(int scheme, uint32_t nx, uint64_t n, bool stats, int &direct, int &rows)
+void step_occupancy_f32(int scheme, uint32_t nx, uint64_t ns, bool stats, int &direct, int &rows)
 {
-    if (fits32(n)) step_occupancy_t<float, float, uint32_t>(scheme, nx, stats, direct, rows);
+    if (fits32(ns)) step_occupancy_t<float, float, uint32_t>(scheme, nx, stats, direct, rows);
     else step_occupancy_t<float, float, uint64_t>(scheme, nx, stats, direct, rows);
 }
 

@@ -669,7 +669,7 @@ __global__ void __launch_bounds__(kBlock, FLBM_MIN_BLOCKS) k_step(S *__restrict_
         totals_init(tot);
         __syncthreads();
     }
-    const I N = I(a.n);
+    const I N = I(a.ns);   // slab stride
     uint32_t it = 0;
     for (uint64_t ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x, ++it) {
         // CTA-uniform: every thread walks the same chunks
@@ -840,7 +840,7 @@ __device__ __forceinline__ S *row_segment(S *g, const StepArgs<R> &a, int d, uin
         if (cz > 0) zz = z ? z - 1 : a.nz - 1;
         if (cz < 0) zz = (z + 1 < a.nz) ? z + 1 : 0;
     }
-    return g + (uint64_t(slot) * a.n + (uint64_t(zz) * a.ny + yy) * a.nx);
+    return g + (uint64_t(slot) * a.ns + (uint64_t(zz) * a.ny + yy) * a.nx);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)

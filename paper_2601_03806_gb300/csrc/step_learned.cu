@@ -96,7 +96,7 @@ __device__ __forceinline__ void stage_node(const float *g, float *stage, const S
 {
     if (s.active) {
         const Nbr<I> nb(s.x, s.y, s.z, a.nx, a.ny, a.nz);
-        const I N = I(a.n);
+        const I N = I(a.ns);   // slab stride
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_step_learned(float *__restri
     float acc[NSTAT];
 #pragma unroll
     for (int s = 0; s < NSTAT; ++s) acc[s] = 0.0f;
-    const I N = I(a.n);
+    const I N = I(a.ns);   // slab stride
     for (uint64_t sc = blockIdx.x; sc < nsuper; sc += gridDim.x) {
         const Site cur = site_of(w, a);
         w = advance(w, step, a);
@@ -240,7 +240,7 @@ bool fits32(uint64_t n) { return n * kQ < (1ull << 32); }
 cudaError_t launch_step_learned(float *g, const StepArgs<float> &a, const LearnArgs &L, bool odd, bool stats,
                                 int grid, cudaStream_t s)
 {
-    if (fits32(a.n)) return launch_t<uint32_t>(g, a, L, odd, stats, grid, s);
+    if (fits32(a.ns)) return launch_t<uint32_t>(g, a, L, odd, stats, grid, s);
     return launch_t<uint64_t>(g, a, L, odd, stats, grid, s);
 }
 

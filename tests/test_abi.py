@@ -101,11 +101,37 @@ def test_noalloc_validation_before_device(F, kw, step, parity, code):
     assert F.flbm_last_error(None)
 
 
-def test_state_bytes_and_params(F):
-    p = F.make_params(512, 512, 512, 0.6, 1e-5)
-    assert F.flbm_state_bytes(C.byref(p)) == 27 * 512 ** 3 * 4
-    p = F.make_params(16, 16, 16, 0.8, 1e-4, precision=F.FLBM_FP64)
-    assert F.flbm_state_bytes(C.byref(p)) == 27 * 16 ** 3 * 8
+def _slab_stride(F, p, es):
+    nbytes = F.flbm_state_bytes(C.byref(p))
+    assert nbytes % (27 * es) == 0
+    return nbytes // (27 * es)
+
+
+@pytest.mark.parametrize("pad", [None, "0", "2048", "1048576"])
+def test_state_bytes_and_params(F, pad, monkeypatch):
+    """27 slabs of ns elements: N rounded up to 64 elements, plus 1 MiB for
+    slabs of 32 MiB and more, or the FLBM_SLAB_PAD bytes when that is set; a
+    pad that is no multiple of 128 bytes is ignored."""
+    if pad is None:
+        monkeypatch.delenv("FLBM_SLAB_PAD", raising=False)
+    else:
+        monkeypatch.setenv("FLBM_SLAB_PAD", pad)
+    for (nx, ny, nz), prec, es in (((512, 512, 512), 1, 4), ((16, 16, 16), 0, 8), ((130, 3, 2), 2, 2)):
+        p = F.make_params(nx, ny, nz, 0.8, 1e-4, precision=prec)
+        n = nx * ny * nz
+        ns = _slab_stride(F, p, es)
+        if pad is None:
+            # 1 MiB pad for slabs of 32 MiB and more, none below
+            big = n * es >= 32 << 20
+            assert ns == (n + 63) // 64 * 64 + ((1 << 20) // es if big else 0)
+        else:
+            assert ns == (n + 63) // 64 * 64 + int(pad) // es
+    monkeypatch.setenv("FLBM_SLAB_PAD", "100")
+    p = F.make_params(64, 4, 4, 0.8, 1e-4)
+    monkeypatch.delenv("FLBM_SLAB_PAD")
+    ns_default = _slab_stride(F, p, 4)
+    monkeypatch.setenv("FLBM_SLAB_PAD", "100")
+    assert _slab_stride(F, p, 4) == ns_default
     p.tau = 0.4
     assert F.flbm_state_bytes(C.byref(p)) == 0
 

@@ -34,6 +34,14 @@ def _sums_from_stats(st, n, rho0):
                      mean[2] * n, mean[3] * n, *sq])
 
 
+def _slabs(flbm, lat, n):
+    """The context's 27 population slabs (FP32) as a [27, n] view of its
+    torch buffer, whose slab stride flbm_state_bytes gives."""
+    import torch
+    ns = int(flbm.flbm_state_bytes(C.byref(lat.params))) // (27 * 4)
+    return lat._buf.view(torch.float32).view(27, ns)[:, :n]
+
+
 def _call(flbm, params, state, t, sums, stream):
     return flbm.flbm_step_noalloc(C.byref(params), C.c_void_p(state.data_ptr()), t, t % 2,
                                   C.c_void_p(sums.data_ptr()), C.c_void_p(stream))
@@ -56,7 +64,7 @@ def test_noalloc_step_matches_flbm_step_and_oracle(oracle_mod, scheme, shape):
                        precision=flbm.FLBM_FP32, stats_every=1, torch_memory=True)
     ref.set_populations(f0)
     torch.cuda.synchronize()
-    state = ref._buf.clone()          # the caller's own copy of the raw state
+    state = _slabs(flbm, ref, n).clone(memory_format=torch.contiguous_format)   # the caller's own 27 unpadded slabs
     sums = torch.zeros(13, dtype=torch.float64, device="cuda")
     stream = ref.stream.cuda_stream
     box = oracle_mod.Box(nx, ny, nz, tau, kT, rho0=rho0, seed=seed, scheme=scheme)
@@ -71,7 +79,7 @@ def test_noalloc_step_matches_flbm_step_and_oracle(oracle_mod, scheme, shape):
         ref.step(1)
         box.step(1)
         torch.cuda.synchronize()
-        assert torch.equal(state, ref._buf), t
+        assert torch.equal(state, _slabs(flbm, ref, n)), t
         st = ref.stats()
         assert st["step"] == t
         s = sums.cpu().numpy()
@@ -101,11 +109,11 @@ def test_noalloc_flags_cleared_between_calls(oracle_mod):
                        torch_memory=True)
     ref.set_populations(f0)
     torch.cuda.synchronize()
-    clean = ref._buf.clone()
+    clean = _slabs(flbm, ref, nx * ny * nz).clone(memory_format=torch.contiguous_format)
     sums = torch.zeros(13, dtype=torch.float64, device="cuda")
     stream = ref.stream.cuda_stream
     bad = clean.clone()
-    bad.view(torch.float32)[5 * nx * ny * nz + 77] = float("nan")
+    bad[5, 77] = float("nan")
     assert _call(flbm, ref.params, bad, 0, sums, stream) == flbm.FLBM_E_UNSTABLE
     assert _call(flbm, ref.params, clean.clone(), 0, sums, stream) == flbm.FLBM_OK
     torch.cuda.synchronize()
