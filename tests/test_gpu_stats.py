@@ -43,9 +43,11 @@ def test_gmf_equipartition_and_er(F, oracle_mod, tau):
     assert np.all(np.abs(er - 1) < 0.02), er
 
 
-@pytest.mark.parametrize("tau", [0.55, 1.0])
+@pytest.mark.parametrize("tau", [0.51, 0.55, 1.0, 5.0])
 def test_gmf_equipartition_fp16_storage(F, tau):
-    """FP16 deviation storage keeps equipartition and ER within 2 %."""
+    """FP16 deviation storage keeps equipartition and ER within the 1 % gate
+    of FP32 (measured at 128^3: within 0.05 %, equal to FP32's values to
+    five digits on the same noise stream)."""
     n, kT, rho0 = 128, 1e-5, 1.0
     g = F.Lattice(n, n, n, tau, kT, rho0=rho0, seed=31, precision=2)
     g.init_thermal(32)
@@ -54,8 +56,8 @@ def test_gmf_equipartition_fp16_storage(F, tau):
     g.step(2000)
     s = g.stats()
     u2 = np.array(s["u2_avg"]) / (kT / rho0)
-    assert np.all(np.abs(u2 - 1) < 0.02), u2
-    assert np.all(np.abs(np.array(s["er"]) - 1) < 0.02), s["er"]
+    assert np.all(np.abs(u2 - 1) < 0.01), u2
+    assert np.all(np.abs(np.array(s["er"]) - 1) < 0.01), s["er"]
 
 
 def test_gmf_flat_structure_factor(F, oracle_mod):
