@@ -14,6 +14,8 @@ persistent kernel per step.
   launch shape the benchmark times: sampled replicas against the oracle.
 * Statistics per replica, the autotuner's reset, the replica restrictions,
   and failure reports naming the replica.
+* The full config-4 run (the mixed workload, 5000 steps): equipartition and
+  ER of every replica within 1 %, and flat class-averaged structure factors.
 """
 import time
 
@@ -295,4 +297,46 @@ def test_replica_structure_factor_matches_single_box(F):
         assert np.array_equal(ca, cb)
         assert np.allclose(Sa, Sb, rtol=1e-5, atol=1e-30), obs
     box.close()
+    ens.close()
+
+
+def test_config4_5000_steps_statistics(F):
+    """The mixed ensemble over the full run (5000 steps after an invariant-
+    measure start, statistics every step): every replica meets the 1 %
+    equipartition gate and keeps its four ER ratios within 1 %, and the
+    structure factors of each size class, averaged over its replicas (one
+    snapshot each), are flat at their Sec. III values (3, 3, 5, 1) rho0 kT:
+    the class mean over shells within 1 %, every shell within five standard
+    errors of a mean of cnt/2 independent exponential variables per replica
+    (the squared modulus of a Gaussian Fourier amplitude, k and -k paired)."""
+    params = mixed_workload(F)
+    ens = F.Ensemble(params)
+    thermal(ens)
+    ens.step(1)
+    for rep in ens.replicas:
+        rep.stats_reset()
+    ens.step(5000)
+    sizes = np.array([p.nx for p in params])
+    for r, rep in enumerate(ens.replicas):
+        s = rep.stats()
+        assert s["n_samples"] == 5000
+        u2 = np.array(s["u2_avg"]) / 1e-5
+        assert np.all(np.abs(u2 - 1) < 0.01), (r, u2)
+        assert np.all(np.abs(np.array(s["er"]) - 1) < 0.01), (r, s["er"])
+    theory = np.array([3, 3, 5, 1]) * 1e-5
+    for n in (32, 64, 128):
+        idx = np.where(sizes == n)[0]
+        nsh = n // 2
+        acc = np.zeros((4, nsh))
+        for r in idx:
+            for obs in range(4):
+                S, cnt = ens[r].structure_factor(obs, nsh)
+                acc[obs] += S
+        acc /= len(idx)
+        shells = slice(2, nsh - 2)
+        for obs in range(4):
+            ratio = acc[obs, shells] / theory[obs]
+            assert abs(ratio.mean() - 1) < 0.01, (n, obs, ratio.mean())
+            bound = 5.0 / np.sqrt(0.5 * cnt[shells] * len(idx))
+            assert np.all(np.abs(ratio - 1) < bound), (n, obs, ratio, bound)
     ens.close()
