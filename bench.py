@@ -44,7 +44,7 @@ WORKLOAD = dict(nx=512, ny=512, nz=512, tau=0.6, kT=1e-5, rho0=1.0, seed=2026010
 BYTES_PER_NODE = {"fp32": 27 * 4 * 2, "fp16": 27 * 2 * 2, "fp64": 27 * 8 * 2}
 CS2 = 1.0 / 3.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_rows_f32_gmf_traffic.txt")
-KERNEL_SOURCES = ["step_kernel.cuh", "lattice.cuh", "internal.h", "step_f32.cu"]
+KERNEL_SOURCES = ["step_kernel.cuh", "lattice.cuh", "internal.h", "step_f32.cu", "step_f32_paced.cu"]
 TRAFFIC16_FILE = os.path.join(ROOT, "profiles", "k_step_rows_f16_gmf_traffic.txt")
 KERNEL16_SOURCES = ["step_kernel.cuh", "lattice.cuh", "internal.h", "step_f16.cu", "step_f16_nx512.cu"]
 ENS_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_ens_f32_gmf_traffic.txt")
@@ -473,8 +473,10 @@ def run_ours(args, rank, local, ws):
     st_name = {"fp32": "float", "fp16": "__half", "fp64": "double"}[args.precision]
     # FP16 rows of exactly 512 nodes run the kernel with the row length fixed at compile time
     fixed = pairs and args.precision == "fp16" and nx == 512
+    # FP32 two-node rows staged twice (more than 256 nodes) run the PACED instance
+    paced = pairs and args.precision == "fp32" and nx > 256
     kname = ("flbm::k_step_rows<%s,GMF,*,stats,NP=%d%s> (TMA row pipeline, %s)"
-             % (st_name, 2 if pairs else 1, ",NXC=512" if fixed else "",
+             % (st_name, 2 if pairs else 1, ",NXC=512" if fixed else (",PACED" if paced else ""),
                 "two nodes per thread" if pairs else "one node per thread")
              if rows_path else "flbm::k_step<%s,GMF,*,stats> (direct)" % st_name)
     if rows_path and not pairs:

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libflbm.so")
 BUILD = os.path.join(ROOT, "_build")
 SOURCES = ["capi.cu", "aux.cu", "step_f32.cu", "step_f64.cu", "step_f16.cu", "step_f16_nx512.cu",
-           "noalloc.cu",
+           "step_f32_paced.cu", "noalloc.cu",
            "ens_f32.cu", "ens_f16.cu", "ens_f32p.cu", "ens_f16p.cu", "ensemble.cu", "mlp_infer.cu",
            "mlp_train.cu", "step_learned.cu", "mstate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

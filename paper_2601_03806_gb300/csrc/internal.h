@@ -162,6 +162,11 @@ void step_occupancy_f16(int scheme, uint32_t nx, uint64_t ns, bool stats, int &d
 cudaError_t launch_rows_f16_nx512(void *g, const StepArgs<float> &a, int scheme, bool odd, bool stats,
                                   int row_grid, cudaStream_t s);
 int rows_occupancy_f16_nx512(int scheme, bool stats);
+// The PACED FP32 two-node row kernels (step_f32_paced.cu) for rows staged
+// twice, which step_f32.cu calls when rows_paced<float> holds for the box.
+cudaError_t launch_rows_f32_paced(float *g, const StepArgs<float> &a, int scheme, bool odd, bool stats,
+                                  int row_grid, cudaStream_t s);
+int rows_occupancy_f32_paced(int scheme, bool stats, uint32_t nx);
 
 // Step constants shared by flbm_step and flbm_step_noalloc (capi.cu): the
 // Philox round keys, the density used by the noise, and the per-mode

@@ -11,6 +11,8 @@ static bool fits32(uint64_t n) { return n * kQ < (1ull << 32); }
 cudaError_t launch_step_f32(float *g, const StepArgs<float> &a, int scheme, bool odd, bool stats,
                             int grid, int row_grid, cudaStream_t s)
 {
+    if (row_grid > 0 && rows_paced<float>(row_plan<float>(a.nx)))
+        return launch_rows_f32_paced(g, a, scheme, odd, stats, row_grid, s);
     if (fits32(a.ns))
         return launch_step_t<float, float, uint32_t>(g, a, scheme, odd, stats, grid, row_grid, s);
     return launch_step_t<float, float, uint64_t>(g, a, scheme, odd, stats, grid, row_grid, s);
@@ -20,6 +22,7 @@ void step_occupancy_f32(int scheme, uint32_t nx, uint64_t ns, bool stats, int &d
 {
     if (fits32(ns)) step_occupancy_t<float, float, uint32_t>(scheme, nx, stats, direct, rows);
     else step_occupancy_t<float, float, uint64_t>(scheme, nx, stats, direct, rows);
+    if (rows > 0 && rows_paced<float>(row_plan<float>(nx))) rows = rows_occupancy_f32_paced(scheme, stats, nx);
 }
 
 }  // namespace flbm

@@ -826,22 +826,57 @@ __host__ __device__ constexpr size_t row_stage_bytes(uint32_t nx) { return size_
 // (cz+1) for the row (y, z): the even form reads slot c of the row itself,
 // the odd form slot opp(c) of row (y - cy, z - cz).  The same segment later
 // receives the post-collision values of direction -c.
-template <typename S, typename R, bool ODD>
-__device__ __forceinline__ S *row_segment(S *g, const StepArgs<R> &a, int d, uint64_t row)
+// A copy lane moves the same segment d of every row: its slot's offset and
+// its row shift are fixed for the launch.
+struct SegLane {
+    uint64_t slot_off;   // slot * ns
+    int cy, cz;          // the odd form's row shift (0 in the even form)
+};
+template <typename R, bool ODD>
+__device__ __forceinline__ SegLane seg_lane(const StepArgs<R> &a, int d)
 {
-    const uint32_t y = uint32_t(row % a.ny), z = uint32_t(row / a.ny);
     const int cx = d / 9 - 1, cy = (d / 3) % 3 - 1, cz = d % 3 - 1;
-    uint32_t yy = y, zz = z;
-    int slot = slot_of(cx, cy, cz);
-    if (ODD) {
-        slot = slot_of(-cx, -cy, -cz);
-        if (cy > 0) yy = y ? y - 1 : a.ny - 1;
-        if (cy < 0) yy = (y + 1 < a.ny) ? y + 1 : 0;
-        if (cz > 0) zz = z ? z - 1 : a.nz - 1;
-        if (cz < 0) zz = (z + 1 < a.nz) ? z + 1 : 0;
-    }
-    return g + (uint64_t(slot) * a.ns + (uint64_t(zz) * a.ny + yy) * a.nx);
+    SegLane L;
+    L.slot_off = uint64_t(ODD ? slot_of(-cx, -cy, -cz) : slot_of(cx, cy, cz)) * a.ns;
+    L.cy = ODD ? cy : 0;
+    L.cz = ODD ? cz : 0;
+    return L;
 }
+template <typename S, typename R>
+__device__ __forceinline__ S *row_segment(S *g, const StepArgs<R> &a, const SegLane &L, uint32_t y, uint32_t z)
+{
+    uint32_t yy = y, zz = z;
+    if (L.cy > 0) yy = y ? y - 1 : a.ny - 1;
+    if (L.cy < 0) yy = (y + 1 < a.ny) ? y + 1 : 0;
+    if (L.cz > 0) zz = z ? z - 1 : a.nz - 1;
+    if (L.cz < 0) zz = (z + 1 < a.nz) ? z + 1 : 0;
+    return g + (L.slot_off + (uint64_t(zz) * a.ny + yy) * a.nx);
+}
+
+// The same address from the row index (y = row % ny, z = row / ny) and the
+// segment index d, decoded on every call: the copy warp of a PACED kernel.
+template <typename S, typename R, bool ODD>
+__device__ __forceinline__ S *row_segment_paced(S *g, const StepArgs<R> &a, int d, uint64_t row)
+{
+    return row_segment<S, R>(g, a, seg_lane<R, ODD>(a, d), uint32_t(row % a.ny), uint32_t(row / a.ny));
+}
+
+// (y, z) of a CTA's rows blockIdx.x + k gridDim.x, k = 0, 1, ..., stepped
+// without a division per row; the rows end at z >= nz.
+struct RowWalk {
+    uint32_t y, z, dy, dz;
+    __device__ __forceinline__ explicit RowWalk(uint32_t ny)
+        : y(blockIdx.x % ny), z(blockIdx.x / ny), dy(gridDim.x % ny), dz(gridDim.x / ny) {}
+    __device__ __forceinline__ void next(uint32_t ny)
+    {
+        y += dy;
+        z += dz;
+        if (y >= ny) {
+            y -= ny;
+            ++z;
+        }
+    }
+};
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
@@ -861,7 +896,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 // is the constant NXC = a.nx and the CTA has kRowPairCompute compute
 // threads, so every segment offset in the stage is an immediate of the
 // shared-memory access instead of an address computed per access.
-template <typename S, typename R, int SCHEME, bool ODD, bool STATS, int NP, uint32_t NXC = 0>
+// PACED: the copy warp derives every copy's address from the row index
+// (row_segment_paced) instead of walking the rows (RowWalk): the same
+// addresses, issued more slowly.  Launched for the FP32 two-node rows
+// staged twice (288-512 nodes; the HBM-bound 512^3 step), where walking made
+// the step 1.5-2.1 % slower; everywhere else walking is faster (256^3 FP32
+// rows +10.8 %, 512^3 FP16 +2.6 %, 128^3 +8.2 %).
+template <typename S, typename R, int SCHEME, bool ODD, bool STATS, int NP, uint32_t NXC = 0, bool PACED = false>
 __global__ void __launch_bounds__(NP == 2 ? kRowPairCompute + 32 : kRowCompute + 32,
                                   NP == 2 ? row_pair_ctas<S>() : (sizeof(S) <= 4 ? 2 : 1))
     k_step_rows(S *__restrict__ g, const StepArgs<R> a, uint32_t nst_log2)
@@ -878,7 +919,6 @@ __global__ void __launch_bounds__(NP == 2 ? kRowPairCompute + 32 : kRowCompute +
     const uint32_t nc = NXC ? uint32_t(kRowPairCompute) : blockDim.x - 32;   // compute threads
     const uint32_t stage_elems = uint32_t(kQ) * nx;
     const uint32_t seg_bytes = nx * uint32_t(sizeof(S));
-    const uint64_t nrows = uint64_t(a.ny) * a.nz;
     const uint32_t lane = threadIdx.x & 31;
     V acc[NSTAT];
 #pragma unroll
@@ -897,25 +937,30 @@ __global__ void __launch_bounds__(NP == 2 ? kRowPairCompute + 32 : kRowCompute +
     if (threadIdx.x >= nc) {
         // ---------------- producer warp ----------------
         const int d = int(lane);
+        const SegLane L = seg_lane<R, ODD>(a, d < kQ ? d : 0);
+        RowWalk wl(a.ny), ws(a.ny);   // the rows loaded / stored next
+        // PACED: (y, z) from the row index by a division, and the lane's
+        // slot and shift decoded again, before every copy (row_segment_paced)
         uint64_t k = 0;
         bool ok = true;
-        // store of row number kk (this CTA's kk-th row) out of its stage
+        // store of row number kk (this CTA's kk-th row) out of its stage;
+        // called for kk = 0, 1, 2, ... in turn (ws walks along)
         auto store_row = [&](uint64_t kk) {
             const int s = int(kk & st_mask);
             ok = mbar_wait(&empty[s], uint32_t((kk >> nst_log2) & 1));
             if (!ok) return;
-            const uint64_t row = blockIdx.x + kk * gridDim.x;
             if (d < kQ) {
-                bulk_s2g(row_segment<S, R, ODD>(g, a, d, row), stage + size_t(s) * stage_elems + d * nx,
-                         seg_bytes);
+                S *gp = PACED ? row_segment_paced<S, R, ODD>(g, a, d, blockIdx.x + kk * gridDim.x)
+                              : row_segment<S, R>(g, a, L, ws.y, ws.z);
+                bulk_s2g(gp, stage + size_t(s) * stage_elems + d * nx, seg_bytes);
                 bulk_commit();
                 bulk_wait_read_all();
             }
+            ws.next(a.ny);
             __syncwarp();
         };
-        for (;; ++k) {
-            const uint64_t row = blockIdx.x + k * gridDim.x;
-            if (row >= nrows) break;
+        for (;; ++k, wl.next(a.ny)) {
+            if (wl.z >= a.nz) break;
             const int s = int(k & st_mask);
             if (k >= nst) {
                 store_row(k - nst);
@@ -926,9 +971,11 @@ __global__ void __launch_bounds__(NP == 2 ? kRowPairCompute + 32 : kRowCompute +
                 mbar_arrive_expect_tx(&full[s], uint32_t(kQ) * seg_bytes + a.tx_pad);
             }
             __syncwarp();
-            if (d < kQ)
-                bulk_g2s(stage + size_t(s) * stage_elems + d * nx, row_segment<S, R, ODD>(g, a, d, row),
-                         seg_bytes, &full[s]);
+            if (d < kQ) {
+                S *gp = PACED ? row_segment_paced<S, R, ODD>(g, a, d, blockIdx.x + k * gridDim.x)
+                              : row_segment<S, R>(g, a, L, wl.y, wl.z);
+                bulk_g2s(stage + size_t(s) * stage_elems + d * nx, gp, seg_bytes, &full[s]);
+            }
         }
         // drain the last stages
         for (uint64_t kk = (k > nst ? k - nst : 0); ok && kk < k; ++kk) store_row(kk);
@@ -936,12 +983,11 @@ __global__ void __launch_bounds__(NP == 2 ? kRowPairCompute + 32 : kRowCompute +
         if (d < kQ) bulk_wait_all();
     } else if constexpr (NP == 2) {
         // ---------------- compute warps, two nodes per thread ----------------
-        for (uint64_t k = 0;; ++k) {
-            const uint64_t row = blockIdx.x + k * gridDim.x;
-            if (row >= nrows) break;
+        RowWalk w(a.ny);
+        for (uint64_t k = 0;; ++k, w.next(a.ny)) {
+            if (w.z >= a.nz) break;
             const int s = int(k & st_mask);
-            const uint32_t y = uint32_t(row % a.ny), z = uint32_t(row / a.ny);
-            const uint32_t rowbase = nx * (y + a.ny * z);
+            const uint32_t rowbase = nx * (w.y + a.ny * w.z);
             // the outcome is made warp-uniform: warp_flush needs every lane
             if (!__all_sync(0xffffffffu, mbar_wait(&full[s], uint32_t((k >> nst_log2) & 1)))) {
                 if (lane == 0) atomicOr(a.flag, 2u);
@@ -990,12 +1036,11 @@ __global__ void __launch_bounds__(NP == 2 ? kRowPairCompute + 32 : kRowCompute +
         }
     } else {
         // ---------------- compute warps, one node per thread ----------------
-        for (uint64_t k = 0;; ++k) {
-            const uint64_t row = blockIdx.x + k * gridDim.x;
-            if (row >= nrows) break;
+        RowWalk w(a.ny);
+        for (uint64_t k = 0;; ++k, w.next(a.ny)) {
+            if (w.z >= a.nz) break;
             const int s = int(k & st_mask);
-            const uint32_t y = uint32_t(row % a.ny), z = uint32_t(row / a.ny);
-            const uint32_t rowbase = nx * (y + a.ny * z);
+            const uint32_t rowbase = nx * (w.y + a.ny * w.z);
             // the first node's normals are drawn while the row's segments land
             R nz[kNoise];
             if (threadIdx.x < nx) draw_noise(a, rowbase + threadIdx.x, nz);
@@ -1137,19 +1182,27 @@ cudaError_t launch_step_t(S *g, const StepArgs<R> &a, int scheme, bool odd, bool
 // Opts the four row kernels of one variant into kRowMaxSmem bytes of dynamic
 // shared memory and returns the resident CTAs per SM of the larger
 // (reducing, odd-form) one for plan rp.
-template <typename S, typename R, int SC, int NP, uint32_t NXC = 0>
+template <typename S, typename R, int SC, int NP, uint32_t NXC = 0, bool PACED = false>
 int prepare_rows(const RowPlan &rp, bool stats)
 {
     const int dmax = int(kRowMaxSmem);
-    cudaFuncSetAttribute(k_step_rows<S, R, SC, false, false, NP, NXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
-    cudaFuncSetAttribute(k_step_rows<S, R, SC, false, true, NP, NXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
-    cudaFuncSetAttribute(k_step_rows<S, R, SC, true, false, NP, NXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
-    cudaFuncSetAttribute(k_step_rows<S, R, SC, true, true, NP, NXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, false, false, NP, NXC, PACED>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, false, true, NP, NXC, PACED>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, true, false, NP, NXC, PACED>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
+    cudaFuncSetAttribute(k_step_rows<S, R, SC, true, true, NP, NXC, PACED>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
     int nb = 0;
     const cudaError_t e = stats
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<S, R, SC, true, true, NP, NXC>, rp.threads, rp.smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<S, R, SC, true, false, NP, NXC>, rp.threads, rp.smem);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<S, R, SC, true, true, NP, NXC, PACED>, rp.threads, rp.smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<S, R, SC, true, false, NP, NXC, PACED>, rp.threads, rp.smem);
     return (e == cudaSuccess && nb > 0) ? nb : 0;
+}
+
+// Whether a box of row length nx runs the PACED two-node row kernel under
+// plan rp: FP32 storage, two nodes per thread, two stages.
+template <typename S>
+inline bool rows_paced(const RowPlan &rp)
+{
+    return std::is_same<S, float>::value && rp.use && rp.np == 2 && rp.stages_log2 == 1;
 }
 
 // Whether a box of row length nx runs the fixed-length two-node row kernel
@@ -1161,15 +1214,15 @@ inline bool rows_fixed(const RowPlan &rp, uint32_t nx)
     return rp.use && rp.np == 2 && nx == NXC && rp.threads == kRowPairCompute + 32;
 }
 
-// One launch of the fixed-length two-node row kernel; the caller has checked
-// rows_fixed<NXC>(row_plan<S>(a.nx), a.nx).
-template <typename S, typename R, uint32_t NXC>
+// One launch of a fixed-length (NXC) or PACED two-node row kernel; the
+// caller has checked rows_fixed<NXC> / rows_paced<S> on row_plan<S>(a.nx).
+template <typename S, typename R, uint32_t NXC, bool PACED = false>
 cudaError_t launch_rows_fixed(S *g, const StepArgs<R> &a, int scheme, bool odd, bool stats, int row_grid,
                               cudaStream_t s)
 {
     const RowPlan rp = row_plan<S>(a.nx);
 #define FLBM_LAUNCH_FIXED(SC, OD, ST) \
-    k_step_rows<S, R, SC, OD, ST, 2, NXC><<<row_grid, rp.threads, rp.smem, s>>>(g, a, rp.stages_log2)
+    k_step_rows<S, R, SC, OD, ST, 2, NXC, PACED><<<row_grid, rp.threads, rp.smem, s>>>(g, a, rp.stages_log2)
     if (scheme == 0) {
         if (odd) { if (stats) FLBM_LAUNCH_FIXED(0, true, true); else FLBM_LAUNCH_FIXED(0, true, false); }
         else     { if (stats) FLBM_LAUNCH_FIXED(0, false, true); else FLBM_LAUNCH_FIXED(0, false, false); }
@@ -1184,14 +1237,14 @@ cudaError_t launch_rows_fixed(S *g, const StepArgs<R> &a, int scheme, bool odd, 
     return cudaGetLastError();
 }
 
-// prepare_rows for the fixed-length kernels of one scheme.
-template <typename S, typename R, uint32_t NXC>
-int prepare_rows_fixed(int scheme, bool stats)
+// prepare_rows for the fixed-length or PACED kernels of one scheme (rows of nx).
+template <typename S, typename R, uint32_t NXC, bool PACED = false>
+int prepare_rows_fixed(int scheme, bool stats, uint32_t nx = NXC)
 {
-    const RowPlan rp = row_plan<S>(NXC);
-    if (scheme == 0) return prepare_rows<S, R, 0, 2, NXC>(rp, stats);
-    if (scheme == 1) return prepare_rows<S, R, 1, 2, NXC>(rp, stats);
-    return prepare_rows<S, R, 2, 2, NXC>(rp, stats);
+    const RowPlan rp = row_plan<S>(nx);
+    if (scheme == 0) return prepare_rows<S, R, 0, 2, NXC, PACED>(rp, stats);
+    if (scheme == 1) return prepare_rows<S, R, 1, 2, NXC, PACED>(rp, stats);
+    return prepare_rows<S, R, 2, 2, NXC, PACED>(rp, stats);
 }
 
 // Resident CTAs per SM of the larger (reducing, odd-form) variant of each
