@@ -901,7 +901,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 // addresses, issued more slowly.  Launched for the FP32 two-node rows
 // staged twice (288-512 nodes; the HBM-bound 512^3 step), where walking made
 // the step 1.5-2.1 % slower; everywhere else walking is faster (256^3 FP32
-// rows +10.8 %, 512^3 FP16 +2.6 %, 128^3 +8.2 %).
+// +10.8 %, 128^3 FP32 +8.3 %, 512^3 FP16 +2.5 %).
 template <typename S, typename R, int SCHEME, bool ODD, bool STATS, int NP, uint32_t NXC = 0, bool PACED = false>
 __global__ void __launch_bounds__(NP == 2 ? kRowPairCompute + 32 : kRowCompute + 32,
                                   NP == 2 ? row_pair_ctas<S>() : (sizeof(S) <= 4 ? 2 : 1))
